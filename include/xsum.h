@@ -1,0 +1,185 @@
+/*
+ * xsum.h -- C ABI of the GB300 exact FP64 summation library (libxsum.so).
+ *
+ * Every entry point sums IEEE-754 binary64 values EXACTLY and rounds the exact
+ * sum once to the nearest double, ties to even, as in R. M. Neal, "Fast Exact
+ * Summation Using Small and Large Superaccumulators" (2015): abstract and
+ * Introduction (problem statement), section "Exact summation using a small
+ * superaccumulator" (67-chunk accumulator, carry propagation, rounding),
+ * section "Faster exact summation of many terms with a large
+ * superaccumulator" (4096-chunk accumulator, transfers), and the Discussion
+ * (merging partial accumulators; results finite whenever the rounded exact sum
+ * is representable).
+ *
+ * Result rules (identical for every entry point and every launch shape; the
+ * result never depends on order, block size or grid size):
+ *   - any NaN input: the NaN with the largest 51-bit payload, a positive one
+ *     preferred on ties, returned with the quiet bit set;
+ *   - else +Inf and -Inf both present: the quiet NaN 0x7FF8000000000000;
+ *   - else +Inf or -Inf present: that infinity (the finite part is ignored);
+ *   - else an exact zero: -0.0 when there is at least one term and every term
+ *     is -0.0, otherwise +0.0 (an empty sum is +0.0);
+ *   - else the exact sum rounded to nearest, ties to even, +-Inf when its
+ *     magnitude is at least 2^1024 - 2^970.
+ *
+ * Conventions:
+ *   - Pointers named d_* are CUDA device pointers (cudaMalloc, cudaMallocAsync
+ *     or managed memory) of the current device; h_* are host pointers.
+ *     Value arrays must be 8-byte aligned; they need not be 16-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Asynchronous calls only enqueue work on it.
+ *   - The caller owns every buffer and stream; the library never writes its
+ *     inputs and never frees caller memory. Library objects (handles, plans,
+ *     servers) own their own device memory until destroyed.
+ *   - The library keeps a small workspace per (device, stream), created on the
+ *     first call that needs it. Calls on one stream are ordered; do not issue
+ *     two library calls that share a workspace or a handle from two host
+ *     threads at once.
+ *   - Errors: functions return an xs_status and also record it as the calling
+ *     thread's last error (xs_get_last_error). XS_ERR_INVALID_VALUE: n < 0,
+ *     misaligned pointer, malformed offsets detected on the host, bad option;
+ *     XS_ERR_INVALID_POINTER: NULL where data is needed, or a host pointer where
+ *     a device pointer is required; XS_ERR_OUT_OF_MEMORY: a library allocation
+ *     failed; XS_ERR_CUDA: any other CUDA runtime error.
+ *   - There is no CPU fallback: without a usable CUDA device every compute
+ *     call fails with XS_ERR_CUDA.
+ */
+#ifndef XSUM_H
+#define XSUM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum xs_status {
+  XS_OK = 0,
+  XS_ERR_INVALID_VALUE = 1,
+  XS_ERR_INVALID_POINTER = 2,
+  XS_ERR_OUT_OF_MEMORY = 3,
+  XS_ERR_CUDA = 4,
+  XS_ERR_TIMEOUT = 5,
+  XS_ERR_BUDGET = 6,
+  XS_ERR_NOT_SUPPORTED = 7,
+  XS_ERR_NOT_READY = 8
+} xs_status;
+
+/* Accumulation method of a single-array sum. */
+typedef enum xs_method {
+  XS_METHOD_AUTO = 0,  /* tuned choice by size (xs_autotune_sum), else built-in default */
+  XS_METHOD_SMALL = 1, /* per-thread small superaccumulators (small-superaccumulator section) */
+  XS_METHOD_LARGE = 2  /* per-block large superaccumulator + transfers (large section) */
+} xs_method;
+
+/* Version string of the library. */
+const char* xs_version(void);
+
+/* Last status recorded by a call on the calling thread; and its text. */
+xs_status xs_get_last_error(void);
+const char* xs_status_string(xs_status s);
+
+/* ---------------------------------------------------------------------------
+ * Single array
+ * ------------------------------------------------------------------------- */
+
+/* Exact sum of d_values[0..n), rounded once (abstract; Discussion).
+ * Blocks the host until the result is ready (stream-ordered). Returns a quiet
+ * NaN and records the error on failure. */
+double xs_sum(const double* d_values, int64_t n, void* stream);
+
+/* Same, with a status; *h_out receives the result. */
+xs_status xs_sum_ex(const double* d_values, int64_t n, void* stream, double* h_out);
+
+/* Asynchronous form: enqueues one kernel on `stream` that writes the rounded
+ * exact sum to the device double *d_out. `method` is an xs_method. */
+xs_status xs_sum_async(const double* d_values, int64_t n, double* d_out, int method,
+                       void* stream);
+
+/* Asynchronous form with an explicit launch shape (used by the autotuner and
+ * the tests; every shape gives the same bits). method: XS_METHOD_SMALL or
+ * XS_METHOD_LARGE; block: threads per block; unroll: 16-byte loads per thread
+ * per tile; grid: blocks (0 = one wave). XS_ERR_NOT_SUPPORTED for a shape that
+ * is not compiled in (see xs_list_configs). */
+xs_status xs_sum_async_config(const double* d_values, int64_t n, double* d_out, int method,
+                              int block, int unroll, int grid, void* stream);
+
+/* Number of compiled launch shapes, and shape k as (method, block, unroll). */
+int xs_list_configs(int* methods, int* blocks, int* unrolls, int capacity);
+
+/* Host-buffer form: h_values[0..n) stays in host memory; the library copies it
+ * to the device in pipelined chunks (pinned host memory gives full speed) and
+ * accumulates each chunk while the next one is in flight. Blocking. */
+xs_status xs_sum_host(const double* h_values, int64_t n, double* h_out, void* stream);
+
+/* Inexact plain FP64 sum (a comparison baseline only, NOT exact: the rounding
+ * after each addition depends on the launch shape). Writes *d_out. */
+xs_status xs_inexact_sum_async(const double* d_values, int64_t n, double* d_out, void* stream);
+
+/* Times every compiled shape of both methods on this input (CUDA events,
+ * `reps` repetitions after one warm-up, median) and records the fastest as the
+ * XS_METHOD_AUTO choice for arrays of this size class (log2 n) on the current
+ * device. Outputs the winner and its median time in microseconds. */
+xs_status xs_autotune_sum(const double* d_values, int64_t n, int reps, void* stream,
+                          int* best_method, int* best_block, int* best_unroll, float* best_us);
+
+/* ---------------------------------------------------------------------------
+ * Batched segmented sums (CSR)
+ * ------------------------------------------------------------------------- */
+
+/* d_out[k] = exact sum of d_values[d_offsets[k] .. d_offsets[k+1]) for
+ * k < nseg. d_offsets (nseg + 1 int64, device) must start at 0 and never
+ * decrease (not checked on the device). One persistent launch behind a CUDA
+ * graph cached per (values, offsets, nseg, out, stream); asynchronous. The
+ * first call for a new key allocates and captures, so make it outside any
+ * stream capture. */
+xs_status xs_sum_segments(const double* d_values, const int64_t* d_offsets, int64_t nseg,
+                          double* d_out, void* stream);
+
+/* Explicit plan: owns the work lists and the instantiated graph. */
+typedef struct xs_seg_plan_s* xs_seg_plan;
+/* Tunables of the segmented kernel; zero fields take the tuned or default value. */
+typedef struct xs_seg_options {
+  int block;         /* threads per block of the persistent kernel */
+  int unroll;        /* 16-byte loads per thread per tile */
+  int tile_elems;    /* elements per block work item of a long segment */
+  int short_max;     /* segments up to this length are summed by one warp */
+  int carry_tiles;   /* tiles between per-thread carry propagations */
+} xs_seg_options;
+xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const int64_t* d_offsets,
+                             int64_t nseg, double* d_out, const xs_seg_options* opts,
+                             void* stream);
+xs_status xs_seg_plan_launch(xs_seg_plan plan, void* stream); /* replays the graph */
+xs_status xs_seg_plan_launch_direct(xs_seg_plan plan, void* stream); /* same kernels, no graph */
+int xs_seg_plan_kernel_launches(xs_seg_plan plan); /* kernels per launch */
+xs_status xs_seg_plan_destroy(xs_seg_plan plan);
+
+/* Times candidate xs_seg_options on this input and records the fastest for
+ * later plans on this device; writes the winner and its median time. */
+xs_status xs_autotune_segments(const double* d_values, const int64_t* d_offsets, int64_t nseg,
+                               double* d_out, int reps, void* stream, xs_seg_options* best,
+                               float* best_us);
+
+/* ---------------------------------------------------------------------------
+ * Device-resident accumulators (partial sums that are merged exactly,
+ * Discussion; canonical form after carry propagation, small section)
+ * ------------------------------------------------------------------------- */
+
+#define XS_ACC_BYTES 560 /* exported state: 67 int64 chunks + flags + NaN key */
+
+typedef struct xs_acc_s* xs_acc;
+xs_status xs_acc_create(xs_acc* h, void* stream);        /* allocates; value: empty sum */
+xs_status xs_acc_init(xs_acc h, void* stream);           /* reset to the empty sum */
+xs_status xs_acc_add(xs_acc h, const double* d_values, int64_t n, void* stream); /* append */
+xs_status xs_acc_merge(xs_acc dst, xs_acc src, void* stream); /* dst += src; src unchanged */
+xs_status xs_acc_round(xs_acc h, double* d_out, void* stream); /* async; state unchanged */
+xs_status xs_acc_export(xs_acc h, void* h_buf, void* stream); /* XS_ACC_BYTES, blocking */
+xs_status xs_acc_import(xs_acc h, const void* h_buf, void* stream); /* blocking */
+xs_status xs_acc_destroy(xs_acc h);
+void* xs_acc_device_state(xs_acc h); /* device address of the 560-byte state */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XSUM_H */

@@ -1,0 +1,823 @@
+// Single-array exact sums, accumulator handles and the host-buffer pipeline.
+//
+// Kernels:
+//   k_sum_small<BLOCK, UNROLL>  small superaccumulator per thread (Fig. 3),
+//                               carry propagation every <= 2047 adds;
+//   k_sum_large<BLOCK, UNROLL>  large superaccumulator per block (Fig. 4) with
+//                               transfers into a block small accumulator;
+// both stream the input once with 16-byte loads (the small kernel keeps the
+// next tile in registers while it adds the current one), merge their block partial into a global 67-chunk accumulator with
+// 64-bit integer atomics (exact, so the order of arrival does not matter --
+// Discussion, parallel summation), and the last block to finish normalises
+// and rounds (small section, rounding).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "xs_host.hpp"
+
+namespace xs {
+
+struct SumArgs {
+  const double* x;
+  long long n;
+  AccState* g;     // global accumulator: zeroed workspace, or a handle's state
+  double* out;     // mode 0: result
+  int mode;        // 0: round into out and reset g; 1: normalise g in place
+  int carry_tiles; // small kernel: tiles between per-thread carry propagations
+};
+
+// Ticket epilogue: the last block to arrive finishes the sum.
+__device__ void finish_grid(const SumArgs& a) {
+  __shared__ unsigned s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&a.g->ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  __syncthreads();
+  if (!s_last || threadIdx.x >= 32) return;
+  __threadfence();
+  const int lane = threadIdx.x;
+  unsigned long long* ch = reinterpret_cast<unsigned long long*>(a.g->chunk);
+  if (a.mode == 0) {
+    long long v0 = (long long)atomicExch(ch + lane, 0ull);
+    long long v1 = (long long)atomicExch(ch + lane + 32, 0ull);
+    long long v2 = lane < 3 ? (long long)atomicExch(ch + lane + 64, 0ull) : 0;
+    unsigned flags = 0u;
+    unsigned long long key = 0ull;
+    if (lane == 0) {
+      flags = atomicExch(&a.g->flags, 0u);
+      key = atomicExch(&a.g->nan_key, 0ull);
+      atomicExch(&a.g->ticket, 0u);
+    }
+    flags = __shfl_sync(kFull, flags, 0);
+    key = __shfl_sync(kFull, key, 0);
+    const unsigned long long bits = warp_round(v0, v1, v2, flags, key);
+    if (lane == 0) *reinterpret_cast<unsigned long long*>(a.out) = bits;
+  } else {
+    long long v0 = (long long)__ldcg(ch + lane);
+    long long v1 = (long long)__ldcg(ch + lane + 32);
+    long long v2 = lane < 3 ? (long long)__ldcg(ch + lane + 64) : 0;
+    warp_normalize(v0, v1, v2);
+    ch[lane] = (unsigned long long)v0;
+    ch[lane + 32] = (unsigned long long)v1;
+    if (lane < 3) ch[lane + 64] = (unsigned long long)v2;
+    if (lane == 0) a.g->ticket = 0u;
+  }
+}
+
+// Split of the input into an optional unaligned head element, 16-byte pairs
+// and an optional tail element.
+struct Split {
+  int head;
+  bool tail;
+  long long npairs;
+  const ulonglong2* xv;
+};
+__device__ __forceinline__ Split split_input(const double* x, long long n) {
+  Split s;
+  s.head = (((uintptr_t)x & 15u) != 0u && n > 0) ? 1 : 0;
+  const long long body = n - s.head;
+  s.npairs = body >> 1;
+  s.tail = (body & 1) != 0;
+  s.xv = reinterpret_cast<const ulonglong2*>(x + s.head);
+  return s;
+}
+
+template <int BLOCK, int UNROLL>
+__device__ __forceinline__ void load_tile(const Split& sp, long long t, int tid, ulonglong2* buf) {
+  const long long base = t * (long long)(BLOCK * UNROLL) + tid;
+#pragma unroll
+  for (int u = 0; u < UNROLL; ++u) {
+    const long long p = base + (long long)u * BLOCK;
+    // padding with -0 adds nothing and leaves the signed-zero record alone
+    buf[u] = (p < sp.npairs) ? ld_stream(sp.xv + p) : make_ulonglong2(kNegZero, kNegZero);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small superaccumulator kernel
+// ---------------------------------------------------------------------------
+
+// Block partial -> global accumulator, plus the special-value record.
+template <int BLOCK>
+__device__ __forceinline__ void block_small_to_global(const long long* sm, const SumArgs& a,
+                                                      unsigned flags, unsigned long long nkey) {
+  unsigned long long* g = reinterpret_cast<unsigned long long*>(a.g->chunk);
+  block_chunk_sums<BLOCK>(sm, [&](int c, long long v) {
+    if (v != 0) atomicAdd(g + c, (unsigned long long)v);
+  });
+  flags = __reduce_or_sync(kFull, flags);
+  nkey = warp_max_ull(nkey);
+  if ((threadIdx.x & 31) == 0) {
+    if (flags) atomicOr(&a.g->flags, flags);
+    if (nkey) atomicMax(&a.g->nan_key, nkey);
+  }
+}
+
+template <int BLOCK, int UNROLL>
+__global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
+  extern __shared__ __align__(16) long long smem_small[];
+  const int tid = threadIdx.x;
+  SmallThread T;
+  T.acc = smem_small + tid;
+  for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
+
+  const Split sp = split_input(a.x, a.n);
+  if (blockIdx.x == 0 && tid == 0) {
+    const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
+    if (sp.head) T.one<BLOCK>(xb[0]);
+    if (sp.tail) T.one<BLOCK>(xb[a.n - 1]);
+  }
+  const long long ntiles = (sp.npairs + (long long)(BLOCK * UNROLL) - 1) / (BLOCK * UNROLL);
+  long long t = blockIdx.x;
+  ulonglong2 cur[UNROLL];
+  if (t < ntiles) load_tile<BLOCK, UNROLL>(sp, t, tid, cur);
+  int since = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    ulonglong2 nxt[UNROLL];
+    const long long tn = t + gridDim.x;
+    if (tn < ntiles) load_tile<BLOCK, UNROLL>(sp, tn, tid, nxt);
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) T.two<BLOCK>(cur[u].x, cur[u].y);
+    if (++since >= a.carry_tiles) {
+      sacc_propagate(T.acc, BLOCK);
+      since = 0;
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) cur[u] = nxt[u];
+  }
+  __syncthreads();
+  unsigned f = T.flags();
+  if (blockIdx.x == 0 && tid == 0 && a.n > 0) f |= kFlagAny;
+  block_small_to_global<BLOCK>(smem_small, a, f, T.nkey);
+  finish_grid(a);
+}
+
+// ---------------------------------------------------------------------------
+// Large superaccumulator kernel
+// ---------------------------------------------------------------------------
+
+template <int BLOCK, int UNROLL>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_sum_large(SumArgs a) {
+  static_assert(BLOCK * UNROLL * 2 <= kLCountMax, "a tile must not exceed one chunk's adds");
+  static_assert(UNROLL * 2 <= 32, "failure mask is 32 bits");
+  extern __shared__ __align__(16) unsigned char smem_large[];
+  LargeSmem& L = *reinterpret_cast<LargeSmem*>(smem_large);
+  const int tid = threadIdx.x;
+  large_init(L, tid, BLOCK);
+  __syncthreads();
+
+  const Split sp = split_input(a.x, a.n);
+  if (blockIdx.x == 0) {  // unaligned head and odd tail, with the special path
+    const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
+    unsigned long long hb = 0ull, tb = 0ull;
+    bool fh = false, ft = false;
+    if (tid == 0) {
+      if (sp.head) { hb = xb[0]; fh = !large_add(L, hb); }
+      if (sp.tail) { tb = xb[a.n - 1]; ft = !large_add(L, tb); }
+    }
+    if (__syncthreads_or(fh || ft)) {
+      if (fh) large_fix(L, hb);
+      if (ft) large_fix(L, tb);
+      __syncthreads();
+      if (fh) large_readd(L, hb);
+      if (ft) large_readd(L, tb);
+      __syncthreads();
+    }
+  }
+
+  // Several blocks share an SM, so one tile of loads in flight per thread is
+  // enough to cover HBM latency; no register double buffer here.
+  const long long ntiles = (sp.npairs + (long long)(BLOCK * UNROLL) - 1) / (BLOCK * UNROLL);
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    ulonglong2 cur[UNROLL];
+    load_tile<BLOCK, UNROLL>(sp, t, tid, cur);
+    unsigned fail = 0u;
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      if (!large_add(L, cur[u].x)) fail |= 1u << (2 * u);
+      if (!large_add(L, cur[u].y)) fail |= 1u << (2 * u + 1);
+    }
+    if (__syncthreads_or(fail != 0u)) {
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        if (fail & (1u << (2 * u))) large_fix(L, cur[u].x);
+        if (fail & (1u << (2 * u + 1))) large_fix(L, cur[u].y);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        if (fail & (1u << (2 * u))) large_readd(L, cur[u].x);
+        if (fail & (1u << (2 * u + 1))) large_readd(L, cur[u].y);
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  large_flush(L, tid, BLOCK);
+  __syncthreads();
+  if (tid < kSChunks) {
+    const long long v = L.sacc[tid];
+    if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.g->chunk[tid]),
+                          (unsigned long long)v);
+  }
+  if (tid == 0) {
+    unsigned f = L.flags;
+    if (blockIdx.x == 0 && a.n > 0) f |= kFlagAny;
+    if (f) atomicOr(&a.g->flags, f);
+    if (L.nan_key) atomicMax(&a.g->nan_key, L.nan_key);
+  }
+  finish_grid(a);
+}
+
+// ---------------------------------------------------------------------------
+// Accumulator-handle kernels
+// ---------------------------------------------------------------------------
+
+// dst += src (chunkwise integer add of normalised accumulators, Discussion),
+// flags OR-ed, NaN keys maximised, then renormalised. One warp.
+__global__ void k_acc_merge(AccState* dst, const AccState* src) {
+  const int lane = threadIdx.x;
+  long long v0 = dst->chunk[lane] + src->chunk[lane];
+  long long v1 = dst->chunk[lane + 32] + src->chunk[lane + 32];
+  long long v2 = lane < 3 ? dst->chunk[lane + 64] + src->chunk[lane + 64] : 0;
+  warp_normalize(v0, v1, v2);
+  dst->chunk[lane] = v0;
+  dst->chunk[lane + 32] = v1;
+  if (lane < 3) dst->chunk[lane + 64] = v2;
+  if (lane == 0) {
+    dst->flags |= src->flags;
+    if (src->nan_key > dst->nan_key) dst->nan_key = src->nan_key;
+  }
+}
+
+// Rounded value of an accumulator; the state is left unchanged. One warp.
+__global__ void k_acc_round(const AccState* s, double* out) {
+  const int lane = threadIdx.x;
+  const long long v0 = s->chunk[lane];
+  const long long v1 = s->chunk[lane + 32];
+  const long long v2 = lane < 3 ? s->chunk[lane + 64] : 0;
+  const unsigned long long bits = warp_round(v0, v1, v2, s->flags, s->nan_key);
+  if (lane == 0) *reinterpret_cast<unsigned long long*>(out) = bits;
+}
+
+// ---------------------------------------------------------------------------
+// Inexact FP64 sum, for comparison only.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_inexact_sum(const double* x, long long n, double* out,
+                                                     double* partial, unsigned* ticket) {
+  const Split sp = split_input(x, n);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; p + stride < sp.npairs; p += 2 * stride) {
+    const ulonglong2 a = ld_stream(sp.xv + p);
+    const ulonglong2 b = ld_stream(sp.xv + p + stride);
+    s0 += __longlong_as_double((long long)a.x);
+    s1 += __longlong_as_double((long long)a.y);
+    s2 += __longlong_as_double((long long)b.x);
+    s3 += __longlong_as_double((long long)b.y);
+  }
+  for (; p < sp.npairs; p += stride) {
+    const ulonglong2 a = ld_stream(sp.xv + p);
+    s0 += __longlong_as_double((long long)a.x);
+    s1 += __longlong_as_double((long long)a.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (sp.head) s2 += x[0];
+    if (sp.tail) s3 += x[n - 1];
+  }
+  double s = (s0 + s1) + (s2 + s3);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  __shared__ unsigned s_last;
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < 8; ++w) b += ws[w];
+    partial[blockIdx.x] = b;
+    __threadfence();
+    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    double tot = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(partial + b);
+    *out = tot;
+    *ticket = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+namespace {
+
+thread_local xs_status g_last = XS_OK;
+
+typedef void (*SumKernel)(SumArgs);
+
+struct KernelEntry {
+  int method, block, unroll;
+  SumKernel fn;
+  size_t smem;
+};
+
+template <int B>
+constexpr size_t small_smem() { return (size_t)B * kSChunks * sizeof(long long); }
+
+const KernelEntry kKernels[] = {
+    {XS_METHOD_SMALL, 128, 4, k_sum_small<128, 4>, small_smem<128>()},
+    {XS_METHOD_SMALL, 128, 8, k_sum_small<128, 8>, small_smem<128>()},
+    {XS_METHOD_SMALL, 256, 4, k_sum_small<256, 4>, small_smem<256>()},
+    {XS_METHOD_SMALL, 256, 8, k_sum_small<256, 8>, small_smem<256>()},
+    {XS_METHOD_SMALL, 384, 4, k_sum_small<384, 4>, small_smem<384>()},
+    {XS_METHOD_SMALL, 384, 8, k_sum_small<384, 8>, small_smem<384>()},
+    {XS_METHOD_LARGE, 256, 4, k_sum_large<256, 4>, sizeof(LargeSmem)},
+    {XS_METHOD_LARGE, 256, 8, k_sum_large<256, 8>, sizeof(LargeSmem)},
+    {XS_METHOD_LARGE, 128, 8, k_sum_large<128, 8>, sizeof(LargeSmem)},
+};
+constexpr int kNumKernels = sizeof(kKernels) / sizeof(kKernels[0]);
+
+std::mutex g_ctx_mu;
+std::map<int, DeviceCtx*> g_ctx;
+
+int find_kernel(int method, int block, int unroll) {
+  for (int k = 0; k < kNumKernels; ++k)
+    if (kKernels[k].method == method && kKernels[k].block == block && kKernels[k].unroll == unroll)
+      return k;
+  return -1;
+}
+
+int size_class(int64_t n) {
+  int c = 0;
+  while (c < 62 && (int64_t(1) << (c + 1)) <= n) ++c;
+  return c;
+}
+
+}  // namespace
+
+xs_status set_error(xs_status s) {
+  g_last = s;
+  return s;
+}
+
+xs_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return set_error(XS_OK);
+  cudaGetLastError();  // clear the sticky-free error state
+  return set_error(e == cudaErrorMemoryAllocation ? XS_ERR_OUT_OF_MEMORY : XS_ERR_CUDA);
+}
+
+xs_status check_device_ptr(const void* p) {
+  if (p == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(XS_ERR_INVALID_POINTER);
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return set_error(XS_ERR_INVALID_POINTER);
+  return XS_OK;
+}
+
+DeviceCtx* device_ctx(xs_status* st) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    *st = from_cuda(e);
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  auto it = g_ctx.find(dev);
+  if (it != g_ctx.end()) {
+    *st = XS_OK;
+    return it->second;
+  }
+  DeviceCtx* c = new DeviceCtx();
+  c->device = dev;
+  e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete c;
+    *st = from_cuda(e);
+    return nullptr;
+  }
+  c->occupancy.resize(kNumKernels, 1);
+  for (int k = 0; k < kNumKernels; ++k) {
+    e = cudaFuncSetAttribute(kKernels[k].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kKernels[k].smem);
+    if (e != cudaSuccess) {
+      delete c;
+      *st = from_cuda(e);
+      return nullptr;
+    }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kKernels[k].fn, kKernels[k].block,
+                                                      kKernels[k].smem);
+    if (e != cudaSuccess) {
+      delete c;
+      *st = from_cuda(e);
+      return nullptr;
+    }
+    c->occupancy[k] = occ > 0 ? occ : 1;
+  }
+  g_ctx[dev] = c;
+  *st = XS_OK;
+  return c;
+}
+
+Workspace* workspace(DeviceCtx* ctx, cudaStream_t s, xs_status* st) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->ws.find(s);
+  if (it != ctx->ws.end()) {
+    *st = XS_OK;
+    return it->second;
+  }
+  Workspace* w = new Workspace();
+  cudaError_t e = cudaMalloc(&w->acc, 2 * sizeof(AccState) + 64);
+  if (e == cudaSuccess) e = cudaMemset(w->acc, 0, 2 * sizeof(AccState) + 64);
+  if (e == cudaSuccess) {
+    w->acc_host = w->acc + 1;
+    w->d_out = reinterpret_cast<double*>(w->acc + 2);
+    e = cudaMallocHost(&w->h_out, sizeof(double));
+  }
+  if (e != cudaSuccess) {
+    if (w->acc) cudaFree(w->acc);
+    delete w;
+    *st = from_cuda(e);
+    return nullptr;
+  }
+  ctx->ws[s] = w;
+  *st = XS_OK;
+  return w;
+}
+
+SumShape default_shape(DeviceCtx* ctx, int64_t n) {
+  auto it = ctx->tuned_sum.find(size_class(n));
+  if (it != ctx->tuned_sum.end()) return it->second;
+  if (n < (int64_t(1) << 20)) return SumShape{XS_METHOD_SMALL, 128, 4};
+  return SumShape{XS_METHOD_LARGE, 256, 8};
+}
+
+xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState* target,
+                     double* d_out, int mode, SumShape shape, int grid, cudaStream_t s) {
+  const int k = find_kernel(shape.method, shape.block, shape.unroll);
+  if (k < 0) return set_error(XS_ERR_NOT_SUPPORTED);
+  const KernelEntry& K = kKernels[k];
+  const long long tile_pairs = (long long)K.block * K.unroll;
+  const long long npairs = n / 2;
+  const long long ntiles = std::max<long long>(1, (npairs + tile_pairs - 1) / tile_pairs);
+  long long g = grid > 0 ? grid : (long long)ctx->num_sms * ctx->occupancy[k];
+  g = std::max<long long>(1, std::min<long long>(g, ntiles));
+  SumArgs a;
+  a.x = d_values;
+  a.n = n;
+  a.g = target;
+  a.out = d_out;
+  a.mode = mode;
+  a.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * K.unroll));
+  K.fn<<<(unsigned)g, K.block, K.smem, s>>>(a);
+  XS_TRY_CUDA(cudaGetLastError());
+  return XS_OK;
+}
+
+}  // namespace xs
+
+using namespace xs;
+
+extern "C" {
+
+const char* xs_version(void) { return "xsum-gb300 0.1 (sm_103a)"; }
+
+xs_status xs_get_last_error(void) { return g_last; }
+
+const char* xs_status_string(xs_status s) {
+  switch (s) {
+    case XS_OK: return "ok";
+    case XS_ERR_INVALID_VALUE: return "invalid value";
+    case XS_ERR_INVALID_POINTER: return "invalid pointer";
+    case XS_ERR_OUT_OF_MEMORY: return "out of memory";
+    case XS_ERR_CUDA: return "CUDA error";
+    case XS_ERR_TIMEOUT: return "timeout";
+    case XS_ERR_BUDGET: return "over budget";
+    case XS_ERR_NOT_SUPPORTED: return "not supported";
+    case XS_ERR_NOT_READY: return "not ready";
+  }
+  return "unknown status";
+}
+
+int xs_list_configs(int* methods, int* blocks, int* unrolls, int capacity) {
+  for (int k = 0; k < kNumKernels && k < capacity; ++k) {
+    if (methods) methods[k] = kKernels[k].method;
+    if (blocks) blocks[k] = kKernels[k].block;
+    if (unrolls) unrolls[k] = kKernels[k].unroll;
+  }
+  return kNumKernels;
+}
+
+static xs_status check_values(const double* d_values, int64_t n) {
+  if (n < 0) return set_error(XS_ERR_INVALID_VALUE);
+  if (n == 0) return XS_OK;
+  if (((uintptr_t)d_values & 7u) != 0u) return set_error(XS_ERR_INVALID_VALUE);
+  return check_device_ptr(d_values);
+}
+
+xs_status xs_sum_async_config(const double* d_values, int64_t n, double* d_out, int method,
+                              int block, int unroll, int grid, void* stream) {
+  xs_status st = check_values(d_values, n);
+  if (st != XS_OK) return st;
+  if ((st = check_device_ptr(d_out)) != XS_OK) return st;
+  if (((uintptr_t)d_out & 7u) != 0u) return set_error(XS_ERR_INVALID_VALUE);
+  if (grid < 0) return set_error(XS_ERR_INVALID_VALUE);
+  cudaStream_t s = as_stream(stream);
+  if (n == 0) {
+    XS_TRY_CUDA(cudaMemsetAsync(d_out, 0, sizeof(double), s));
+    return set_error(XS_OK);
+  }
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  SumShape shape = (method == XS_METHOD_AUTO) ? default_shape(ctx, n)
+                                              : SumShape{method, block, unroll};
+  if (method != XS_METHOD_AUTO && (block == 0 || unroll == 0)) {
+    SumShape d = default_shape(ctx, n);
+    if (d.method != method) d = (method == XS_METHOD_SMALL) ? SumShape{method, 128, 4}
+                                                            : SumShape{method, 256, 8};
+    shape = d;
+  }
+  Workspace* w = workspace(ctx, s, &st);
+  if (!w) return st;
+  st = launch_sum(ctx, d_values, n, w->acc, d_out, 0, shape, grid, s);
+  if (st != XS_OK) return st;
+  return set_error(XS_OK);
+}
+
+xs_status xs_sum_async(const double* d_values, int64_t n, double* d_out, int method,
+                       void* stream) {
+  if (method < XS_METHOD_AUTO || method > XS_METHOD_LARGE) return set_error(XS_ERR_INVALID_VALUE);
+  return xs_sum_async_config(d_values, n, d_out, method, 0, 0, 0, stream);
+}
+
+xs_status xs_sum_ex(const double* d_values, int64_t n, void* stream, double* h_out) {
+  if (h_out == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  xs_status st = check_values(d_values, n);
+  if (st != XS_OK) return st;
+  if (n == 0) {
+    *h_out = 0.0;
+    return set_error(XS_OK);
+  }
+  cudaStream_t s = as_stream(stream);
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  Workspace* w = workspace(ctx, s, &st);
+  if (!w) return st;
+  st = launch_sum(ctx, d_values, n, w->acc, w->d_out, 0, default_shape(ctx, n), 0, s);
+  if (st != XS_OK) return st;
+  XS_TRY_CUDA(cudaMemcpyAsync(w->h_out, w->d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  XS_TRY_CUDA(cudaStreamSynchronize(s));
+  *h_out = *w->h_out;
+  return set_error(XS_OK);
+}
+
+double xs_sum(const double* d_values, int64_t n, void* stream) {
+  double r = 0.0;
+  if (xs_sum_ex(d_values, n, stream, &r) != XS_OK) {
+    unsigned long long qnan = 0x7FF8000000000000ull;
+    std::memcpy(&r, &qnan, sizeof r);
+  }
+  return r;
+}
+
+xs_status xs_sum_host(const double* h_values, int64_t n, double* h_out, void* stream) {
+  if (h_out == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  if (n < 0) return set_error(XS_ERR_INVALID_VALUE);
+  if (n > 0 && h_values == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  if (((uintptr_t)h_values & 7u) != 0u) return set_error(XS_ERR_INVALID_VALUE);
+  if (n == 0) {
+    *h_out = 0.0;
+    return set_error(XS_OK);
+  }
+  xs_status st;
+  cudaStream_t s = as_stream(stream);
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  Workspace* w = workspace(ctx, s, &st);
+  if (!w) return st;
+  const size_t chunk = size_t(1) << 23;  // 8 Mi doubles (64 MiB) per staging slot
+  if (w->stage_elems == 0) {
+    for (int k = 0; k < 2; ++k) {
+      XS_TRY_CUDA(cudaMalloc(&w->stage[k], chunk * sizeof(double)));
+      XS_TRY_CUDA(cudaEventCreateWithFlags(&w->full[k], cudaEventDisableTiming));
+      XS_TRY_CUDA(cudaEventCreateWithFlags(&w->free_[k], cudaEventDisableTiming));
+    }
+    XS_TRY_CUDA(cudaStreamCreateWithFlags(&w->copy_stream, cudaStreamNonBlocking));
+    w->stage_elems = chunk;
+  }
+  XS_TRY_CUDA(cudaMemsetAsync(w->acc_host, 0, sizeof(AccState), s));
+  // the copy stream must not overwrite a slot before the reset above is done
+  XS_TRY_CUDA(cudaEventRecord(w->free_[0], s));
+  XS_TRY_CUDA(cudaEventRecord(w->free_[1], s));
+  const SumShape shape = default_shape(ctx, (int64_t)std::min<size_t>(chunk, (size_t)n));
+  int64_t done = 0;
+  for (int k = 0; done < n; ++k) {
+    const int slot = k & 1;
+    const int64_t m = std::min<int64_t>((int64_t)chunk, n - done);
+    XS_TRY_CUDA(cudaStreamWaitEvent(w->copy_stream, w->free_[slot], 0));
+    XS_TRY_CUDA(cudaMemcpyAsync(w->stage[slot], h_values + done, (size_t)m * sizeof(double),
+                                cudaMemcpyHostToDevice, w->copy_stream));
+    XS_TRY_CUDA(cudaEventRecord(w->full[slot], w->copy_stream));
+    XS_TRY_CUDA(cudaStreamWaitEvent(s, w->full[slot], 0));
+    st = launch_sum(ctx, w->stage[slot], m, w->acc_host, nullptr, 1, shape, 0, s);
+    if (st != XS_OK) return st;
+    XS_TRY_CUDA(cudaEventRecord(w->free_[slot], s));
+    done += m;
+  }
+  k_acc_round<<<1, 32, 0, s>>>(w->acc_host, w->d_out);
+  XS_TRY_CUDA(cudaGetLastError());
+  XS_TRY_CUDA(cudaMemcpyAsync(w->h_out, w->d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  XS_TRY_CUDA(cudaStreamSynchronize(s));
+  *h_out = *w->h_out;
+  return set_error(XS_OK);
+}
+
+xs_status xs_inexact_sum_async(const double* d_values, int64_t n, double* d_out, void* stream) {
+  xs_status st = check_values(d_values, n);
+  if (st != XS_OK) return st;
+  if ((st = check_device_ptr(d_out)) != XS_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  if (n == 0) {
+    XS_TRY_CUDA(cudaMemsetAsync(d_out, 0, sizeof(double), s));
+    return set_error(XS_OK);
+  }
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  Workspace* w = workspace(ctx, s, &st);
+  if (!w) return st;
+  static thread_local double* partial = nullptr;
+  static thread_local int partial_dev = -1;
+  const int grid = ctx->num_sms * 8;
+  if (partial == nullptr || partial_dev != ctx->device) {
+    XS_TRY_CUDA(cudaMalloc(&partial, (size_t)grid * sizeof(double) + 64));
+    XS_TRY_CUDA(cudaMemset(partial, 0, (size_t)grid * sizeof(double) + 64));
+    partial_dev = ctx->device;
+  }
+  unsigned* ticket = reinterpret_cast<unsigned*>(partial + grid);
+  k_inexact_sum<<<grid, 256, 0, s>>>(d_values, n, d_out, partial, ticket);
+  XS_TRY_CUDA(cudaGetLastError());
+  return set_error(XS_OK);
+}
+
+xs_status xs_autotune_sum(const double* d_values, int64_t n, int reps, void* stream,
+                          int* best_method, int* best_block, int* best_unroll, float* best_us) {
+  xs_status st = check_values(d_values, n);
+  if (st != XS_OK) return st;
+  if (n == 0 || reps <= 0) return set_error(XS_ERR_INVALID_VALUE);
+  cudaStream_t s = as_stream(stream);
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  Workspace* w = workspace(ctx, s, &st);
+  if (!w) return st;
+  cudaEvent_t e0, e1;
+  XS_TRY_CUDA(cudaEventCreate(&e0));
+  XS_TRY_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  SumShape win{XS_METHOD_SMALL, 128, 4};
+  std::vector<float> times;
+  for (int k = 0; k < kNumKernels; ++k) {
+    const SumShape sh{kKernels[k].method, kKernels[k].block, kKernels[k].unroll};
+    st = launch_sum(ctx, d_values, n, w->acc, w->d_out, 0, sh, 0, s);  // warm-up
+    if (st != XS_OK) return st;
+    times.clear();
+    for (int r = 0; r < reps; ++r) {
+      XS_TRY_CUDA(cudaEventRecord(e0, s));
+      st = launch_sum(ctx, d_values, n, w->acc, w->d_out, 0, sh, 0, s);
+      if (st != XS_OK) return st;
+      XS_TRY_CUDA(cudaEventRecord(e1, s));
+      XS_TRY_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      XS_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      times.push_back(ms);
+    }
+    std::sort(times.begin(), times.end());
+    const float med = times[times.size() / 2];
+    if (med < best) {
+      best = med;
+      win = sh;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->tuned_sum[size_class(n)] = win;
+  }
+  if (best_method) *best_method = win.method;
+  if (best_block) *best_block = win.block;
+  if (best_unroll) *best_unroll = win.unroll;
+  if (best_us) *best_us = best * 1000.f;
+  return set_error(XS_OK);
+}
+
+// ----------------------------- accumulator handles --------------------------
+
+struct xs_acc_s {
+  AccState* d = nullptr;
+  int device = -1;
+};
+
+xs_status xs_acc_create(xs_acc* h, void* stream) {
+  if (h == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  xs_status st;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  xs_acc a = new xs_acc_s();
+  cudaError_t e = cudaMalloc(&a->d, sizeof(AccState));
+  if (e != cudaSuccess) {
+    delete a;
+    return from_cuda(e);
+  }
+  a->device = ctx->device;
+  e = cudaMemsetAsync(a->d, 0, sizeof(AccState), as_stream(stream));
+  if (e != cudaSuccess) {
+    cudaFree(a->d);
+    delete a;
+    return from_cuda(e);
+  }
+  *h = a;
+  return set_error(XS_OK);
+}
+
+xs_status xs_acc_init(xs_acc h, void* stream) {
+  if (h == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  XS_TRY_CUDA(cudaMemsetAsync(h->d, 0, sizeof(AccState), as_stream(stream)));
+  return set_error(XS_OK);
+}
+
+xs_status xs_acc_add(xs_acc h, const double* d_values, int64_t n, void* stream) {
+  if (h == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  xs_status st = check_values(d_values, n);
+  if (st != XS_OK) return st;
+  if (n == 0) return set_error(XS_OK);
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  st = launch_sum(ctx, d_values, n, h->d, nullptr, 1, default_shape(ctx, n), 0,
+                  as_stream(stream));
+  if (st != XS_OK) return st;
+  return set_error(XS_OK);
+}
+
+xs_status xs_acc_merge(xs_acc dst, xs_acc src, void* stream) {
+  if (dst == nullptr || src == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  if (dst == src) return set_error(XS_ERR_INVALID_VALUE);
+  k_acc_merge<<<1, 32, 0, as_stream(stream)>>>(dst->d, src->d);
+  XS_TRY_CUDA(cudaGetLastError());
+  return set_error(XS_OK);
+}
+
+xs_status xs_acc_round(xs_acc h, double* d_out, void* stream) {
+  if (h == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  xs_status st = check_device_ptr(d_out);
+  if (st != XS_OK) return st;
+  k_acc_round<<<1, 32, 0, as_stream(stream)>>>(h->d, d_out);
+  XS_TRY_CUDA(cudaGetLastError());
+  return set_error(XS_OK);
+}
+
+xs_status xs_acc_export(xs_acc h, void* h_buf, void* stream) {
+  if (h == nullptr || h_buf == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  cudaStream_t s = as_stream(stream);
+  XS_TRY_CUDA(cudaMemcpyAsync(h_buf, h->d, sizeof(AccState), cudaMemcpyDeviceToHost, s));
+  XS_TRY_CUDA(cudaStreamSynchronize(s));
+  return set_error(XS_OK);
+}
+
+xs_status xs_acc_import(xs_acc h, const void* h_buf, void* stream) {
+  if (h == nullptr || h_buf == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  AccState tmp;
+  std::memcpy(&tmp, h_buf, sizeof tmp);
+  for (int c = 0; c < kSChunks - 1; ++c)
+    if (tmp.chunk[c] < 0 || tmp.chunk[c] > 0xFFFFFFFFll) return set_error(XS_ERR_INVALID_VALUE);
+  if (tmp.chunk[kSChunks - 1] < -(1ll << 33) || tmp.chunk[kSChunks - 1] > (1ll << 33))
+    return set_error(XS_ERR_INVALID_VALUE);
+  tmp.ticket = 0u;
+  cudaStream_t s = as_stream(stream);
+  XS_TRY_CUDA(cudaMemcpyAsync(h->d, &tmp, sizeof(AccState), cudaMemcpyHostToDevice, s));
+  XS_TRY_CUDA(cudaStreamSynchronize(s));
+  return set_error(XS_OK);
+}
+
+xs_status xs_acc_destroy(xs_acc h) {
+  if (h == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  cudaFree(h->d);
+  delete h;
+  return set_error(XS_OK);
+}
+
+void* xs_acc_device_state(xs_acc h) { return h ? (void*)h->d : nullptr; }
+
+}  // extern "C"

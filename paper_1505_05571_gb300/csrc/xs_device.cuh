@@ -1,0 +1,433 @@
+// Device-side building blocks of the exact FP64 summation library.
+//
+// Method: R. M. Neal, "Fast Exact Summation Using Small and Large
+// Superaccumulators" (2015).
+//   * small superaccumulator: 67 signed 64-bit chunks, chunk i weighing
+//     2^(32 i - 1075), 32-bit overlap (section "Exact summation using a small
+//     superaccumulator", Fig. 2 and Fig. 3);
+//   * carry propagation at most every 2^11 - 1 adds (same section);
+//   * large superaccumulator: one 64-bit chunk per sign+exponent with a count of
+//     remaining adds, transferred into the small one (section "Faster exact
+//     summation of many terms with a large superaccumulator", Fig. 4);
+//   * merge of partial accumulators and one final rounding (Discussion).
+//
+// GPU layout: every thread owns a private small superaccumulator in shared
+// memory, laid out [chunk][thread] so a warp's 64-bit accesses never conflict;
+// a block owns one large superaccumulator in shared memory, updated with shared
+// atomics; block partials meet in one global accumulator through 64-bit integer
+// atomics (exact and order-free), and the last block to finish rounds.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace xs {
+
+constexpr int kSChunks = 67;        // small superaccumulator chunks
+constexpr int kLowExpBits = 5;      // low exponent bits: position inside a chunk
+constexpr int kCarryInterval = 2047;  // adds of <= 2^52-1 between propagations
+constexpr int kLChunks = 4096;      // large superaccumulator: one per sign+exponent
+constexpr int kLCountMax = 4096;    // adds to one large chunk before a transfer
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+constexpr unsigned long long kPosInf = 0x7FF0000000000000ull;
+constexpr unsigned long long kNegInf = 0xFFF0000000000000ull;
+constexpr unsigned long long kDefaultNaN = 0x7FF8000000000000ull;
+constexpr unsigned long long kNegZero = 0x8000000000000000ull;
+constexpr unsigned long long kPayloadMask = 0x0007FFFFFFFFFFFFull;
+constexpr unsigned long long kMantMask = 0x000FFFFFFFFFFFFFull;
+
+// Record of the terms that do not enter the chunks (Inf and NaN fields of the
+// small superaccumulator, Fig. 3) plus what decides the sign of a zero.
+enum : unsigned {
+  kFlagPosInf = 1u,
+  kFlagNegInf = 2u,
+  kFlagNotNegZero = 4u,  // some term is not -0
+  kFlagAny = 8u,         // at least one term
+};
+
+// Device-resident accumulator: the canonical small superaccumulator plus the
+// special-value record. 560 bytes; also the export format of a handle.
+struct __align__(16) AccState {
+  long long chunk[kSChunks];
+  unsigned flags;
+  unsigned ticket;  // completion counter of the kernel writing into it; 0 at rest
+  unsigned long long nan_key;  // 0 = no NaN seen
+  unsigned long long reserved;
+};
+static_assert(sizeof(AccState) == 560, "AccState layout");
+
+// NaN choice (order-independent): largest 51-bit payload, positive sign on
+// ties; the key is maximised with atomicMax.
+__device__ __forceinline__ unsigned long long nan_key_of(unsigned long long b) {
+  return ((((b & kPayloadMask) << 1) | ((b >> 63) ^ 1ull)) + 1ull);
+}
+__device__ __forceinline__ unsigned long long nan_from_key(unsigned long long k) {
+  k -= 1ull;
+  return ((k & 1ull) ? 0ull : kNegZero) | 0x7FF8000000000000ull | (k >> 1);
+}
+
+// Streaming 16-byte load that does not allocate in L1.
+__device__ __forceinline__ ulonglong2 ld_stream(const ulonglong2* p) {
+  ulonglong2 v;
+  asm("ld.global.nc.L1::no_allocate.L2::256B.v2.u64 {%0, %1}, [%2];"
+      : "=l"(v.x), "=l"(v.y)
+      : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_stream1(const unsigned long long* p) {
+  unsigned long long v;
+  asm("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+// --------------------------------------------------------------------------
+// Small superaccumulator, one per thread, chunks strided by `stride` longs.
+// --------------------------------------------------------------------------
+
+// Add one finite double (given as its two 32-bit halves) to the thread's
+// small superaccumulator (Fig. 3, branch-free sign as the Discussion
+// suggests). Zeros add nothing; the caller handles e == 2047.
+// 53-bit significand M, e_eff = max(e, 1), i = e_eff >> 5, l = e_eff & 31;
+// the low 32 bits of M << l go to chunk i, the rest (< 2^52) to chunk i+1.
+__device__ __forceinline__ void sacc_add(long long* __restrict__ a, int stride,
+                                         unsigned lo, unsigned hi) {
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned mh = (hi & 0xFFFFFu) | (e != 0u ? 0x100000u : 0u);
+  const unsigned ee = e + (e == 0u ? 1u : 0u);
+  const unsigned i = ee >> kLowExpBits;
+  const unsigned l = ee & 31u;
+  const unsigned p0 = lo << l;                    // bits 0..31 of M << l
+  const unsigned q0 = __funnelshift_l(lo, mh, l);  // bits 32..63
+  const unsigned q1 = __funnelshift_l(mh, 0u, l);  // bits 64..95
+  const long long s = (long long)((int)hi >> 31);  // 0 or -1
+  const long long vlo = (long long)(unsigned long long)p0;
+  const long long vhi = (long long)(((unsigned long long)q1 << 32) | q0);
+  long long* c = a + (int)i * stride;
+  c[0] += (vlo ^ s) - s;
+  c[stride] += (vhi ^ s) - s;
+}
+
+// Per-thread state of the small-superaccumulator path: the chunks plus the
+// Inf/NaN record and what decides the sign of an exact zero.
+struct SmallThread {
+  long long* acc;  // this thread's chunks, stride BLOCK
+  unsigned and_hi = 0x80000000u, or_hi = 0x80000000u, or_lo = 0u;
+  unsigned sflags = 0u;
+  unsigned long long nkey = 0ull;
+
+  __device__ __forceinline__ void special(unsigned long long b) {
+    if (b & kMantMask) {
+      const unsigned long long k = nan_key_of(b);
+      nkey = k > nkey ? k : nkey;
+    } else {
+      sflags |= (b >> 63) ? kFlagNegInf : kFlagPosInf;
+    }
+  }
+  template <int BLOCK>
+  __device__ __forceinline__ void one(unsigned long long b) {
+    const unsigned lo = (unsigned)b, hi = (unsigned)(b >> 32);
+    and_hi &= hi;
+    or_hi |= hi;
+    or_lo |= lo;
+    if (((hi >> 20) & 0x7FFu) == 0x7FFu) {
+      special(b);
+    } else {
+      sacc_add(acc, BLOCK, lo, hi);
+    }
+  }
+  template <int BLOCK>
+  __device__ __forceinline__ void two(unsigned long long a, unsigned long long b) {
+    const unsigned alo = (unsigned)a, ahi = (unsigned)(a >> 32);
+    const unsigned blo = (unsigned)b, bhi = (unsigned)(b >> 32);
+    and_hi &= ahi & bhi;
+    or_hi |= ahi | bhi;
+    or_lo |= alo | blo;
+    const bool sa = ((ahi >> 20) & 0x7FFu) == 0x7FFu;
+    const bool sb = ((bhi >> 20) & 0x7FFu) == 0x7FFu;
+    if (__builtin_expect(sa || sb, 0)) {
+      if (sa) special(a); else sacc_add(acc, BLOCK, alo, ahi);
+      if (sb) special(b); else sacc_add(acc, BLOCK, blo, bhi);
+    } else {
+      sacc_add(acc, BLOCK, alo, ahi);
+      sacc_add(acc, BLOCK, blo, bhi);
+    }
+  }
+  __device__ __forceinline__ unsigned flags() const {
+    return sflags | ((and_hi != 0x80000000u || or_hi != 0x80000000u || or_lo != 0u)
+                         ? kFlagNotNegZero : 0u);
+  }
+};
+
+// Carry propagation (small-superaccumulator section): from chunk 0 upward,
+// move the signed high 32 bits of each chunk into the next; the top chunk
+// keeps its own. Afterwards chunks 0..65 lie in [0, 2^32).
+__device__ __forceinline__ void sacc_propagate(long long* __restrict__ a, int stride) {
+  long long carry = 0;
+#pragma unroll 6
+  for (int c = 0; c < kSChunks - 1; ++c) {
+    const long long v = a[c * stride] + carry;
+    a[c * stride] = v & 0xFFFFFFFFll;
+    carry = v >> 32;
+  }
+  a[(kSChunks - 1) * stride] += carry;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_max_ull(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Block reduction of the per-thread chunks without a final per-thread carry
+// propagation: chunk c of every thread (|c| < 2^63) splits into its low 32 bits
+// and its signed high part, and the high part is owed to chunk c+1. Warp w
+// handles chunks w, w + BLOCK/32, ...; lane 0 hands the two warp sums to
+// `emit(chunk, value)`, which adds them into the target accumulator (global or
+// shared). Sums stay below 2^41 in magnitude for BLOCK <= 512.
+template <int BLOCK, typename Emit>
+__device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = BLOCK / 32;
+  for (int c = warp; c < kSChunks; c += NW) {
+    long long lo = 0, hi = 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const long long v = sm[c * BLOCK + k * 32 + lane];
+      lo += v & 0xFFFFFFFFll;
+      hi += v >> 32;
+    }
+    lo = warp_sum_ll(lo);
+    hi = warp_sum_ll(hi);
+    if (lane == 0) {
+      if (c == kSChunks - 1) {
+        emit(c, lo + hi * 4294967296ll);
+      } else {
+        emit(c, lo);
+        emit(c + 1, hi);
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Warp-level normalisation and rounding of a 67-chunk accumulator.
+// Lane L holds chunks L (v0), L+32 (v1) and L+64 (v2, lanes 0..2 only).
+// --------------------------------------------------------------------------
+
+// Parallel carry propagation: every round moves each chunk's signed high part
+// one chunk up. After two rounds all carries are -1, 0 or +1 and travel one
+// chunk per round, so at most 69 rounds reach the canonical form.
+__device__ __forceinline__ void warp_normalize(long long& v0, long long& v1, long long& v2) {
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < 80; ++it) {
+    const long long c0 = v0 >> 32;
+    const long long c1 = v1 >> 32;
+    const long long c2 = (lane < 2) ? (v2 >> 32) : 0;  // chunk 66 keeps its high part
+    if (!__any_sync(kFull, (c0 | c1 | c2) != 0)) break;
+    v0 &= 0xFFFFFFFFll;
+    v1 &= 0xFFFFFFFFll;
+    if (lane < 2) v2 &= 0xFFFFFFFFll;
+    long long u0 = __shfl_up_sync(kFull, c0, 1);
+    long long u1 = __shfl_up_sync(kFull, c1, 1);
+    long long u2 = __shfl_up_sync(kFull, c2, 1);
+    const long long w0 = __shfl_sync(kFull, c0, 31);
+    const long long w1 = __shfl_sync(kFull, c1, 31);
+    if (lane == 0) {
+      u0 = 0;
+      u1 = w0;
+      u2 = w1;
+    }
+    v0 += u0;
+    v1 += u1;
+    v2 += u2;
+  }
+}
+
+__device__ __forceinline__ unsigned lanes_below(int x) {
+  return x <= 0 ? 0u : (x >= 32 ? kFull : ((1u << x) - 1u));
+}
+
+// Correct rounding, ties to even (small-superaccumulator section on
+// rounding; overflow as in the Discussion). All 32 lanes call it; the
+// returned bit pattern is valid in every lane.
+__device__ __noinline__ static unsigned long long warp_round(long long v0, long long v1, long long v2,
+                                         unsigned flags, unsigned long long nan_key) {
+  if (nan_key != 0ull) return nan_from_key(nan_key);
+  if ((flags & (kFlagPosInf | kFlagNegInf)) == (kFlagPosInf | kFlagNegInf)) return kDefaultNaN;
+  if (flags & kFlagPosInf) return kPosInf;
+  if (flags & kFlagNegInf) return kNegInf;
+  const int lane = threadIdx.x & 31;
+  warp_normalize(v0, v1, v2);
+  const bool neg = __shfl_sync(kFull, v2, 2) < 0;
+  if (neg) {
+    v0 = -v0;
+    v1 = -v1;
+    v2 = -v2;
+    warp_normalize(v0, v1, v2);
+  }
+  const unsigned b0 = __ballot_sync(kFull, v0 != 0);
+  const unsigned b1 = __ballot_sync(kFull, v1 != 0);
+  const unsigned b2 = __ballot_sync(kFull, v2 != 0);
+  if ((b0 | b1 | b2) == 0u) {
+    return ((flags & kFlagAny) && !(flags & kFlagNotNegZero)) ? kNegZero : 0ull;
+  }
+  const int h = b2 ? 64 + 31 - __clz(b2) : (b1 ? 32 + 31 - __clz(b1) : 31 - __clz(b0));
+  auto chunk_at = [&](int k) -> unsigned long long {
+    const int slot = k < 0 ? 0 : (k >> 5);
+    const long long sv = slot == 0 ? v0 : (slot == 1 ? v1 : v2);
+    const long long r = __shfl_sync(kFull, sv, k < 0 ? 0 : (k & 31));
+    return k < 0 ? 0ull : (unsigned long long)r;
+  };
+  const unsigned long long dh = chunk_at(h);
+  const unsigned long long dm = chunk_at(h - 1);
+  const unsigned long long dl = chunk_at(h - 2);
+  const int below = h - 2;
+  const bool sticky_low = ((b0 & lanes_below(below)) | (b1 & lanes_below(below - 32)) |
+                           (b2 & lanes_below(below - 64))) != 0u;
+  (void)lane;
+  unsigned long long bits;
+  const int tb = 63 - __clzll((long long)dh);  // top bit of chunk h
+  const int P = 32 * h + tb;                   // top bit of the magnitude, units 2^-1075
+  if (P < 54) {
+    // |sum| < 2^53 units of 2^-1074: exact, and its pattern is the integer itself.
+    const unsigned long long A = (h >= 1 ? (chunk_at(1) << 32) : 0ull) + chunk_at(0);
+    bits = A >> 1;
+  } else {
+    const unsigned __int128 W = ((unsigned __int128)dh << 64) | ((unsigned __int128)dm << 32) |
+                                (unsigned __int128)dl;
+    unsigned long long q = (unsigned long long)(W >> (tb + 12));  // 53 bits
+    const bool rbit = (unsigned)(W >> (tb + 11)) & 1u;
+    const unsigned __int128 rest_mask = (((unsigned __int128)1) << (tb + 11)) - 1;
+    const bool sticky = sticky_low || ((W & rest_mask) != 0);
+    if (rbit && (sticky || (q & 1ull))) q += 1ull;
+    const unsigned long long e = (unsigned long long)(P - 52);  // biased exponent
+    bits = ((e - 1ull) << 52) + q;  // a carry out of q bumps the exponent
+    if (bits >= kPosInf) bits = kPosInf;
+  }
+  return bits | (neg ? kNegZero : 0ull);
+}
+
+// --------------------------------------------------------------------------
+// Large superaccumulator in shared memory, one per block (Fig. 4).
+// --------------------------------------------------------------------------
+
+struct LargeSmem {
+  unsigned long long chunk[kLChunks];  // raw-bit sums; valid only where used
+  int count[kLChunks];                  // adds left before a transfer; -1 = unused
+  unsigned long long used[kLChunks / 64];  // chunks in use
+  unsigned long long used_used;            // non-empty words of `used`
+  long long sacc[kSChunks];                // transfer target: block small accumulator
+  unsigned flags;
+  unsigned pad;
+  unsigned long long nan_key;
+};
+
+__device__ __forceinline__ void large_init(LargeSmem& L, int tid, int nthreads) {
+  for (int k = tid; k < kLChunks; k += nthreads) L.count[k] = -1;
+  for (int k = tid; k < kLChunks / 64; k += nthreads) L.used[k] = 0ull;
+  for (int k = tid; k < kSChunks; k += nthreads) L.sacc[k] = 0;
+  if (tid == 0) {
+    L.used_used = 0ull;
+    L.flags = 0u;
+    L.nan_key = 0ull;
+  }
+}
+
+// Transfer of one large chunk into the block small accumulator (large
+// section): undo the raw sign/exponent bits of the adds not done
+// (index * remaining << 52), add the implicit ones (adds * 2^52) for normal
+// exponents, shift by the low 5 exponent bits and add the three 32-bit pieces
+// to small chunks i, i+1, i+2 with the sign of the index.
+__device__ __forceinline__ void large_transfer(LargeSmem& L, unsigned ix,
+                                               unsigned long long chunkval, int remaining) {
+  const unsigned e = ix & 0x7FFu;
+  const unsigned adds = (unsigned)(kLCountMax - remaining);
+  const unsigned long long sum_m =
+      chunkval + ((unsigned long long)((ix * (unsigned)remaining) & 0xFFFu) << 52);
+  if (adds == 0u) return;
+  if (ix != 0x800u || sum_m != 0ull) atomicOr(&L.flags, kFlagNotNegZero);
+  unsigned __int128 T = sum_m;
+  if (e != 0u) T += ((unsigned __int128)adds) << 52;
+  const unsigned ee = e ? e : 1u;
+  const unsigned i = ee >> kLowExpBits;
+  T <<= (ee & 31u);
+  const long long p0 = (long long)(unsigned)(T);
+  const long long p1 = (long long)(unsigned)(T >> 32);
+  const long long p2 = (long long)(unsigned)(T >> 64);
+  const bool neg = (ix >> 11) != 0u;
+  unsigned long long* s = reinterpret_cast<unsigned long long*>(L.sacc);
+  if (p0) atomicAdd(s + i, (unsigned long long)(neg ? -p0 : p0));
+  if (p1) atomicAdd(s + i + 1, (unsigned long long)(neg ? -p1 : p1));
+  if (p2) atomicAdd(s + i + 2, (unsigned long long)(neg ? -p2 : p2));
+}
+
+// Hot path: count down and add the raw bits (Fig. 4). Returns false when the
+// term needs the special path (first use of the chunk, 4096 adds reached, or
+// Inf/NaN, whose count stays negative).
+__device__ __forceinline__ bool large_add(LargeSmem& L, unsigned long long bits) {
+  const unsigned ix = (unsigned)(bits >> 52);
+  const int old = atomicAdd(&L.count[ix], -1);
+  if (old > 0) {
+    atomicAdd(&L.chunk[ix], bits);
+    return true;
+  }
+  return false;
+}
+
+// Special path, phase 1 (after a barrier): record Inf/NaN, and for each chunk
+// that refused a term, exactly one thread transfers it (4096 adds done) or
+// marks it used (first use), clears it and resets its count.
+__device__ __forceinline__ void large_fix(LargeSmem& L, unsigned long long bits) {
+  const unsigned ix = (unsigned)(bits >> 52);
+  if ((ix & 0x7FFu) == 0x7FFu) {
+    if (bits & kMantMask) {
+      atomicMax(&L.nan_key, nan_key_of(bits));
+    } else {
+      atomicOr(&L.flags, (ix >> 11) ? kFlagNegInf : kFlagPosInf);
+    }
+    atomicOr(&L.flags, kFlagNotNegZero);
+    atomicExch(&L.count[ix], -1);
+    return;
+  }
+  const int old = atomicExch(&L.count[ix], kLCountMax);
+  if (old == kLCountMax) return;  // another thread fixed this chunk
+  const unsigned long long ubit = 1ull << (ix & 63u);
+  if (L.used[ix >> 6] & ubit) {
+    large_transfer(L, ix, L.chunk[ix], 0);
+  } else {
+    atomicOr(&L.used[ix >> 6], ubit);
+    atomicOr(&L.used_used, 1ull << (ix >> 6));
+  }
+  L.chunk[ix] = 0ull;
+}
+
+// Special path, phase 2 (after another barrier): the refused finite terms are
+// added; their chunks have just been reset, so the count cannot run out.
+__device__ __forceinline__ void large_readd(LargeSmem& L, unsigned long long bits) {
+  const unsigned ix = (unsigned)(bits >> 52);
+  if ((ix & 0x7FFu) == 0x7FFu) return;
+  atomicAdd(&L.count[ix], -1);
+  atomicAdd(&L.chunk[ix], bits);
+}
+
+// Final transfer of every used chunk (large section: the used flags let the
+// scan skip unused chunks). All threads of the block call it.
+__device__ __forceinline__ void large_flush(LargeSmem& L, int tid, int nthreads) {
+  for (int ix = tid; ix < kLChunks; ix += nthreads) {
+    if (!((L.used_used >> (ix >> 6)) & 1ull)) continue;
+    if (!((L.used[ix >> 6] >> (ix & 63)) & 1ull)) continue;
+    const int rem = L.count[ix];
+    large_transfer(L, (unsigned)ix, L.chunk[ix], rem > 0 ? rem : 0);
+  }
+}
+
+}  // namespace xs

@@ -1,0 +1,76 @@
+// Host-side runtime shared by the library's translation units: error state,
+// per-device context, per-stream workspaces and launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "../../include/xsum.h"
+#include "xs_device.cuh"
+
+namespace xs {
+
+xs_status set_error(xs_status s);
+xs_status from_cuda(cudaError_t e);  // records and maps a CUDA error
+
+#define XS_TRY_CUDA(call)                        \
+  do {                                           \
+    cudaError_t _e = (call);                     \
+    if (_e != cudaSuccess) return from_cuda(_e); \
+  } while (0)
+
+// Device pointer check (cudaPointerGetAttributes): host or unregistered
+// memory is rejected.
+xs_status check_device_ptr(const void* p);
+
+// Work space of one (device, stream) pair. Allocated zeroed; every kernel that
+// uses `acc` leaves it zeroed again (the last block resets what it read).
+struct Workspace {
+  AccState* acc = nullptr;        // grid accumulator of xs_sum
+  AccState* acc_host = nullptr;   // accumulator of xs_sum_host
+  double* d_out = nullptr;        // device result slot
+  double* h_out = nullptr;        // pinned result slot
+  // xs_sum_host staging ring
+  double* stage[2] = {nullptr, nullptr};
+  size_t stage_elems = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t full[2] = {nullptr, nullptr};
+  cudaEvent_t free_[2] = {nullptr, nullptr};
+};
+
+struct SumShape {
+  int method;
+  int block;
+  int unroll;
+};
+
+struct DeviceCtx {
+  int device = -1;
+  int num_sms = 0;
+  std::mutex mu;
+  std::map<cudaStream_t, Workspace*> ws;
+  // tuned single-array choice per size class (log2 n)
+  std::map<int, SumShape> tuned_sum;
+  // tuned segmented options (one entry; 0 fields = defaults)
+  bool have_tuned_seg = false;
+  xs_seg_options tuned_seg{};
+  std::vector<int> occupancy;  // resident blocks per SM of each compiled shape
+};
+
+DeviceCtx* device_ctx(xs_status* st);  // context of the current device
+Workspace* workspace(DeviceCtx* ctx, cudaStream_t s, xs_status* st);
+
+// Launch of the single-array kernel into a target accumulator.
+// mode 0: round into d_out and reset the target; mode 1: normalise the target
+// in place (accumulator handles).
+xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState* target,
+                     double* d_out, int mode, SumShape shape, int grid, cudaStream_t s);
+SumShape default_shape(DeviceCtx* ctx, int64_t n);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace xs

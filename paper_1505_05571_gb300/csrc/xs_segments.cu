@@ -1,0 +1,596 @@
+// Batched segmented exact sums (CSR): one persistent launch behind a CUDA graph.
+//
+// Each segment is summed exactly and rounded once (abstract; small section on
+// rounding). Work decomposition, computed on the device from the offsets by
+// k_seg_prep:
+//   * long segments (length > short_max) are cut into tiles of tile_elems
+//     elements; a block sums a tile with per-thread small superaccumulators
+//     (Fig. 3). A one-tile segment is rounded by that block; the tiles of a
+//     longer segment meet in a per-segment global accumulator through integer
+//     atomics (partial superaccumulators added exactly, Discussion) and the
+//     last tile to finish rounds;
+//   * short segments are summed by one warp each; segments of at most two
+//     finite terms take a single IEEE addition, which is correctly rounded for
+//     two terms (Discussion).
+// Blocks take long tiles from a global cursor first, then their warps take
+// short segments from a second cursor, so short work fills the tail.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "xs_host.hpp"
+
+namespace xs {
+
+struct SegArgs {
+  const double* x;
+  const long long* off;  // nseg + 1
+  long long nseg;
+  double* out;
+  long long* tile_start;       // nseg + 1: exclusive scan of the tiles of long segments
+  int* slot_of;                // nseg: accumulator slot of a multi-tile segment, else -1
+  long long* short_list;       // nseg: indices of short segments
+  AccState* slots;             // per multi-tile segment
+  unsigned long long* counters;  // [0] tiles, [1] short segments, [2] tile cursor, [3] short cursor
+  long long tile_elems;
+  long long short_max;
+};
+
+// Block-wide exclusive scan of one long long per thread (1024 threads).
+__device__ long long block_exclusive_scan(long long v, long long* total, long long* sbuf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) sbuf[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    long long w = lane < nw ? sbuf[lane] : 0;
+    long long wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < nw) sbuf[lane] = wi - w;  // exclusive warp offsets
+    if (lane == 31) sbuf[32] = wi;
+  }
+  __syncthreads();
+  const long long r = sbuf[warp] + incl - v;
+  *total = sbuf[32];
+  __syncthreads();
+  return r;
+}
+
+// Work lists from the offsets. One block of 1024 threads; thread t owns a
+// contiguous run of segments.
+__global__ void __launch_bounds__(1024) k_seg_prep(SegArgs a) {
+  __shared__ long long sbuf[33];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long per = (a.nseg + nt - 1) / nt;
+  const long long s0 = min((long long)tid * per, a.nseg);
+  const long long s1 = min(s0 + per, a.nseg);
+  long long tiles = 0, nshort = 0, nslot = 0;
+  for (long long s = s0; s < s1; ++s) {
+    const long long L = a.off[s + 1] - a.off[s];
+    if (L > a.short_max) {
+      const long long t = (L + a.tile_elems - 1) / a.tile_elems;
+      tiles += t;
+      nslot += (t > 1);
+    } else {
+      ++nshort;
+    }
+  }
+  long long tot_tiles, tot_short, tot_slot;
+  long long t_off = block_exclusive_scan(tiles, &tot_tiles, sbuf);
+  long long sh_off = block_exclusive_scan(nshort, &tot_short, sbuf);
+  long long sl_off = block_exclusive_scan(nslot, &tot_slot, sbuf);
+  for (long long s = s0; s < s1; ++s) {
+    const long long L = a.off[s + 1] - a.off[s];
+    a.tile_start[s] = t_off;
+    int slot = -1;
+    if (L > a.short_max) {
+      const long long t = (L + a.tile_elems - 1) / a.tile_elems;
+      t_off += t;
+      if (t > 1) slot = (int)(sl_off++);
+    } else {
+      a.short_list[sh_off++] = s;
+    }
+    a.slot_of[s] = slot;
+  }
+  if (tid == 0) {
+    a.tile_start[a.nseg] = tot_tiles;
+    a.counters[0] = (unsigned long long)tot_tiles;
+    a.counters[1] = (unsigned long long)tot_short;
+    a.counters[2] = 0ull;
+    a.counters[3] = 0ull;
+  }
+}
+
+// Adds x[lo, hi) to the per-thread accumulators of `nthr` cooperating threads
+// (rank r among them). 16-byte loads, the next group kept in flight while the
+// current one is added; one unaligned head and one odd tail element.
+template <int BLOCK, int UNROLL>
+__device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x, long long lo,
+                                                 long long hi, int r, int nthr) {
+  const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(x);
+  long long p = lo;
+  if (p < hi && (((uintptr_t)(x + p)) & 15u) != 0u) {
+    if (r == 0) T.one<BLOCK>(xb[p]);
+    ++p;
+  }
+  if (((hi - p) & 1) != 0 && p < hi) {
+    if (r == nthr - 1) T.one<BLOCK>(xb[hi - 1]);
+    --hi;
+  }
+  const long long npairs = (hi - p) >> 1;
+  const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(x + p);
+  const long long step = (long long)UNROLL * nthr;
+  ulonglong2 cur[UNROLL], nxt[UNROLL];
+  long long q = r;
+#pragma unroll
+  for (int u = 0; u < UNROLL; ++u) {
+    const long long k = q + (long long)u * nthr;
+    cur[u] = k < npairs ? ld_stream(xv + k) : make_ulonglong2(kNegZero, kNegZero);
+  }
+  for (; q < npairs; q += step) {
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const long long k = q + step + (long long)u * nthr;
+      nxt[u] = k < npairs ? ld_stream(xv + k) : make_ulonglong2(kNegZero, kNegZero);
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) T.two<BLOCK>(cur[u].x, cur[u].y);
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) cur[u] = nxt[u];
+  }
+}
+
+template <int BLOCK, int UNROLL>
+__global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
+  extern __shared__ __align__(16) long long smem_seg[];
+  __shared__ long long bsum[kSChunks];
+  __shared__ long long s_item;
+  __shared__ unsigned s_flags;
+  __shared__ unsigned long long s_nkey;
+  __shared__ unsigned s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  SmallThread T;
+  T.acc = smem_seg + tid;
+  const long long ntiles = (long long)a.counters[0];
+  const long long nshort = (long long)a.counters[1];
+
+  // ---- phase 1: tiles of long segments, one block each ----
+  for (;;) {
+    if (tid == 0) s_item = (long long)atomicAdd(&a.counters[2], 1ull);
+    if (tid < kSChunks) bsum[tid] = 0;
+    if (tid == 0) {
+      s_flags = 0u;
+      s_nkey = 0ull;
+    }
+    __syncthreads();
+    const long long t = s_item;
+    if (t >= ntiles) break;
+    // segment of tile t: last s with tile_start[s] <= t
+    long long lo_s = 0, hi_s = a.nseg;  // invariant: tile_start[lo_s] <= t < tile_start[hi_s]
+    while (hi_s - lo_s > 1) {
+      const long long mid = (lo_s + hi_s) >> 1;
+      if (a.tile_start[mid] <= t) lo_s = mid; else hi_s = mid;
+    }
+    const long long s = lo_s;
+    const long long first_tile = a.tile_start[s];
+    const long long seg_tiles = a.tile_start[s + 1] - first_tile;
+    const long long seg_lo = a.off[s], seg_hi = a.off[s + 1];
+    const long long lo = seg_lo + (t - first_tile) * a.tile_elems;
+    const long long hi = min(lo + a.tile_elems, seg_hi);
+    for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
+    T.and_hi = 0x80000000u; T.or_hi = 0x80000000u; T.or_lo = 0u; T.sflags = 0u; T.nkey = 0ull;
+    accumulate_range<BLOCK, UNROLL>(T, a.x, lo, hi, tid, BLOCK);
+    __syncthreads();
+    unsigned f = __reduce_or_sync(kFull, T.flags());
+    const unsigned long long k = warp_max_ull(T.nkey);
+    if (lane == 0) {
+      if (f) atomicOr(&s_flags, f);
+      if (k) atomicMax(&s_nkey, k);
+    }
+    if (seg_tiles == 1) {
+      block_chunk_sums<BLOCK>(smem_seg, [&](int c, long long v) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(bsum + c), (unsigned long long)v);
+      });
+      __syncthreads();
+      if (warp == 0) {
+        const unsigned bits = 0u;
+        (void)bits;
+        const unsigned long long r = warp_round(bsum[lane], bsum[lane + 32],
+                                                lane < 3 ? bsum[lane + 64] : 0,
+                                                s_flags | kFlagAny, s_nkey);
+        if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
+      }
+    } else {
+      AccState* g = a.slots + a.slot_of[s];
+      unsigned long long* gc = reinterpret_cast<unsigned long long*>(g->chunk);
+      block_chunk_sums<BLOCK>(smem_seg, [&](int c, long long v) {
+        if (v != 0) atomicAdd(gc + c, (unsigned long long)v);
+      });
+      __syncthreads();
+      if (tid == 0) {
+        if (s_flags) atomicOr(&g->flags, s_flags);
+        if (s_nkey) atomicMax(&g->nan_key, s_nkey);
+        __threadfence();
+        s_last = (atomicAdd(&g->ticket, 1u) == (unsigned)(seg_tiles - 1)) ? 1u : 0u;
+      }
+      __syncthreads();
+      if (s_last && warp == 0) {
+        __threadfence();
+        const long long v0 = (long long)atomicExch(gc + lane, 0ull);
+        const long long v1 = (long long)atomicExch(gc + lane + 32, 0ull);
+        const long long v2 = lane < 3 ? (long long)atomicExch(gc + lane + 64, 0ull) : 0;
+        unsigned fl = 0u;
+        unsigned long long key = 0ull;
+        if (lane == 0) {
+          fl = atomicExch(&g->flags, 0u);
+          key = atomicExch(&g->nan_key, 0ull);
+          atomicExch(&g->ticket, 0u);
+        }
+        fl = __shfl_sync(kFull, fl, 0);
+        key = __shfl_sync(kFull, key, 0);
+        const unsigned long long r = warp_round(v0, v1, v2, fl | kFlagAny, key);
+        if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- phase 2: short segments, one warp each ----
+  const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
+  for (;;) {
+    long long j = 0;
+    if (lane == 0) j = (long long)atomicAdd(&a.counters[3], 1ull);
+    j = __shfl_sync(kFull, j, 0);
+    if (j >= nshort) break;
+    const long long s = a.short_list[j];
+    const long long lo = a.off[s], hi = a.off[s + 1];
+    const long long L = hi - lo;
+    if (L <= 2) {
+      const unsigned long long b0 = L > 0 ? xb[lo] : 0ull;
+      const unsigned long long b1 = L > 1 ? xb[lo + 1] : kNegZero;
+      const bool fin = ((b0 >> 52) & 0x7FFu) != 0x7FFu && ((b1 >> 52) & 0x7FFu) != 0x7FFu;
+      if (L == 0 || fin) {
+        if (lane == 0) {
+          // one IEEE addition is correctly rounded; x + (-0) = x keeps -0 alone
+          const double r = L == 0 ? 0.0 : __dadd_rn(__longlong_as_double((long long)b0),
+                                                  __longlong_as_double((long long)b1));
+          a.out[s] = r;
+        }
+        continue;
+      }
+    }
+    for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
+    T.and_hi = 0x80000000u; T.or_hi = 0x80000000u; T.or_lo = 0u; T.sflags = 0u; T.nkey = 0ull;
+    accumulate_range<BLOCK, 2>(T, a.x, lo, hi, lane, 32);
+    __syncwarp();
+    // lane L gathers chunks L, L+32, L+64 of the warp's 32 accumulators, split
+    // into low and high halves; reads are rotated by lane to avoid conflicts
+    const long long* wbase = smem_seg + warp * 32;
+    long long lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0, lo2 = 0, hi2 = 0;
+    for (int q = 0; q < 32; ++q) {
+      const int src = (q + lane) & 31;
+      const long long u0 = wbase[lane * BLOCK + src];
+      const long long u1 = wbase[(lane + 32) * BLOCK + src];
+      const long long u2 = lane < 3 ? wbase[(lane + 64) * BLOCK + src] : 0;
+      lo0 += u0 & 0xFFFFFFFFll; hi0 += u0 >> 32;
+      lo1 += u1 & 0xFFFFFFFFll; hi1 += u1 >> 32;
+      lo2 += u2 & 0xFFFFFFFFll; hi2 += u2 >> 32;
+    }
+    // high half of chunk c belongs to chunk c+1 (chunk 66 keeps its own)
+    const long long top_hi = (lane == 2) ? hi2 : 0;
+    long long in0 = __shfl_up_sync(kFull, hi0, 1);
+    long long in1 = __shfl_up_sync(kFull, hi1, 1);
+    long long in2 = __shfl_up_sync(kFull, hi2, 1);
+    const long long w0 = __shfl_sync(kFull, hi0, 31);
+    const long long w1 = __shfl_sync(kFull, hi1, 31);
+    if (lane == 0) { in0 = 0; in1 = w0; in2 = w1; }
+    const long long v0 = lo0 + in0;
+    const long long v1 = lo1 + in1;
+    const long long v2 = lane < 3 ? lo2 + in2 + top_hi * 4294967296ll : 0;
+    const unsigned f = __reduce_or_sync(kFull, T.flags()) | kFlagAny;
+    const unsigned long long key = warp_max_ull(T.nkey);
+    const unsigned long long r = warp_round(v0, v1, v2, f, key);
+    if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
+    __syncwarp();
+  }
+}
+
+namespace {
+
+typedef void (*SegKernel)(SegArgs);
+struct SegEntry {
+  int block, unroll;
+  SegKernel fn;
+};
+const SegEntry kSeg[] = {
+    {128, 4, k_seg_main<128, 4>},
+    {192, 4, k_seg_main<192, 4>},
+    {256, 4, k_seg_main<256, 4>},
+    {384, 4, k_seg_main<384, 4>},
+    {192, 8, k_seg_main<192, 8>},
+};
+constexpr int kNumSeg = sizeof(kSeg) / sizeof(kSeg[0]);
+
+int find_seg(int block, int unroll) {
+  for (int k = 0; k < kNumSeg; ++k)
+    if (kSeg[k].block == block && kSeg[k].unroll == unroll) return k;
+  return -1;
+}
+
+size_t seg_smem(int block) { return (size_t)block * kSChunks * sizeof(long long); }
+
+xs_seg_options default_seg_options(DeviceCtx* ctx) {
+  if (ctx->have_tuned_seg) return ctx->tuned_seg;
+  xs_seg_options o;
+  o.block = 192;
+  o.unroll = 4;
+  o.tile_elems = 1 << 18;
+  o.short_max = 4096;
+  o.carry_tiles = 0;
+  return o;
+}
+
+xs_status resolve_options(DeviceCtx* ctx, const xs_seg_options* in, xs_seg_options* out) {
+  xs_seg_options d = default_seg_options(ctx);
+  xs_seg_options o = in ? *in : d;
+  if (o.block == 0) o.block = d.block;
+  if (o.unroll == 0) o.unroll = d.unroll;
+  if (o.tile_elems == 0) o.tile_elems = d.tile_elems;
+  if (o.short_max == 0) o.short_max = d.short_max;
+  if (find_seg(o.block, o.unroll) < 0) return set_error(XS_ERR_NOT_SUPPORTED);
+  // per-thread adds between carry propagations stay within 2047
+  if (o.tile_elems < 2 * o.block || o.tile_elems > 2040LL * o.block) return set_error(XS_ERR_INVALID_VALUE);
+  if (o.short_max < 0 || o.short_max > 2040 * 32) return set_error(XS_ERR_INVALID_VALUE);
+  *out = o;
+  return XS_OK;
+}
+
+}  // namespace
+
+}  // namespace xs
+
+using namespace xs;
+
+struct xs_seg_plan_s {
+  int device = -1;
+  SegArgs args{};
+  xs_seg_options opts{};
+  int kernel = -1;
+  int grid = 0;
+  void* mem = nullptr;  // one allocation for all work lists
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static xs_status plan_enqueue(xs_seg_plan p, cudaStream_t s) {
+  k_seg_prep<<<1, 1024, 0, s>>>(p->args);
+  XS_TRY_CUDA(cudaGetLastError());
+  const SegEntry& K = kSeg[p->kernel];
+  K.fn<<<p->grid, K.block, seg_smem(K.block), s>>>(p->args);
+  XS_TRY_CUDA(cudaGetLastError());
+  return XS_OK;
+}
+
+extern "C" {
+
+xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const int64_t* d_offsets,
+                             int64_t nseg, double* d_out, const xs_seg_options* opts,
+                             void* stream) {
+  if (plan == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  if (nseg <= 0) return set_error(XS_ERR_INVALID_VALUE);
+  if (nseg > (int64_t(1) << 31) - 2) return set_error(XS_ERR_INVALID_VALUE);
+  xs_status st;
+  if ((st = check_device_ptr(d_offsets)) != XS_OK) return st;
+  if ((st = check_device_ptr(d_out)) != XS_OK) return st;
+  if (d_values != nullptr && (st = check_device_ptr(d_values)) != XS_OK) return st;
+  if (((uintptr_t)d_values & 7u) || ((uintptr_t)d_offsets & 7u) || ((uintptr_t)d_out & 7u))
+    return set_error(XS_ERR_INVALID_VALUE);
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  xs_seg_options o;
+  if ((st = resolve_options(ctx, opts, &o)) != XS_OK) return st;
+  const int k = find_seg(o.block, o.unroll);
+  {
+    static bool attr_done[64][kNumSeg] = {};
+    if (ctx->device < 64 && !attr_done[ctx->device][k]) {
+      XS_TRY_CUDA(cudaFuncSetAttribute(kSeg[k].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)seg_smem(o.block)));
+      attr_done[ctx->device][k] = true;
+    }
+  }
+  int occ = 0;
+  XS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kSeg[k].fn, o.block,
+                                                            seg_smem(o.block)));
+  if (occ < 1) return set_error(XS_ERR_NOT_SUPPORTED);
+  xs_seg_plan p = new xs_seg_plan_s();
+  p->device = ctx->device;
+  p->opts = o;
+  p->kernel = k;
+  p->grid = ctx->num_sms * occ;
+  // layout: counters (64 B) | tile_start (nseg+1) | short_list (nseg) | slot_of (nseg) | slots
+  const size_t n = (size_t)nseg;
+  const size_t bytes_ctr = 64;
+  const size_t bytes_ts = (n + 1) * 8, bytes_sl = n * 8, bytes_so = ((n * 4 + 15) / 16) * 16;
+  // multi-tile segments: at most total/tile, and at most nseg
+  const size_t max_slots = n;
+  const size_t bytes_slots = max_slots * sizeof(AccState);
+  const size_t total = bytes_ctr + bytes_ts + bytes_sl + bytes_so + bytes_slots;
+  cudaError_t e = cudaMalloc(&p->mem, total);
+  if (e != cudaSuccess) {
+    delete p;
+    return from_cuda(e);
+  }
+  cudaStream_t s = as_stream(stream);
+  e = cudaMemsetAsync(p->mem, 0, total, s);
+  if (e != cudaSuccess) {
+    cudaFree(p->mem);
+    delete p;
+    return from_cuda(e);
+  }
+  char* base = static_cast<char*>(p->mem);
+  SegArgs& a = p->args;
+  a.x = d_values;
+  a.off = reinterpret_cast<const long long*>(d_offsets);
+  a.nseg = nseg;
+  a.out = d_out;
+  a.counters = reinterpret_cast<unsigned long long*>(base);
+  a.tile_start = reinterpret_cast<long long*>(base + bytes_ctr);
+  a.short_list = reinterpret_cast<long long*>(base + bytes_ctr + bytes_ts);
+  a.slot_of = reinterpret_cast<int*>(base + bytes_ctr + bytes_ts + bytes_sl);
+  a.slots = reinterpret_cast<AccState*>(base + bytes_ctr + bytes_ts + bytes_sl + bytes_so);
+  a.tile_elems = o.tile_elems;
+  a.short_max = o.short_max;
+  // capture prep + main into a graph on a private stream
+  cudaStream_t cs;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // memset done before any replay
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    xs_status qs = plan_enqueue(p, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
+    e = (qs != XS_OK) ? cudaErrorUnknown : e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    if (p->graph) cudaGraphDestroy(p->graph);
+    cudaFree(p->mem);
+    delete p;
+    return from_cuda(e);
+  }
+  *plan = p;
+  return set_error(XS_OK);
+}
+
+xs_status xs_seg_plan_launch(xs_seg_plan p, void* stream) {
+  if (p == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  XS_TRY_CUDA(cudaGraphLaunch(p->exec, as_stream(stream)));
+  return set_error(XS_OK);
+}
+
+xs_status xs_seg_plan_launch_direct(xs_seg_plan p, void* stream) {
+  if (p == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  xs_status st = plan_enqueue(p, as_stream(stream));
+  if (st != XS_OK) return st;
+  return set_error(XS_OK);
+}
+
+int xs_seg_plan_kernel_launches(xs_seg_plan p) { return p ? 2 : 0; }
+
+xs_status xs_seg_plan_destroy(xs_seg_plan p) {
+  if (p == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  cudaFree(p->mem);
+  delete p;
+  return set_error(XS_OK);
+}
+
+}  // extern "C"
+
+namespace {
+std::mutex g_plan_mu;
+std::map<std::tuple<int, const void*, const void*, int64_t, void*, void*>, xs_seg_plan> g_plans;
+}  // namespace
+
+extern "C" {
+
+xs_status xs_sum_segments(const double* d_values, const int64_t* d_offsets, int64_t nseg,
+                          double* d_out, void* stream) {
+  if (nseg < 0) return set_error(XS_ERR_INVALID_VALUE);
+  if (nseg == 0) return set_error(XS_OK);
+  int dev = -1;
+  XS_TRY_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, (const void*)d_values, (const void*)d_offsets, nseg,
+                                   (void*)d_out, stream);
+  xs_seg_plan p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) p = it->second;
+  }
+  if (p == nullptr) {
+    xs_status st = xs_seg_plan_create(&p, d_values, d_offsets, nseg, d_out, nullptr, stream);
+    if (st != XS_OK) return st;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[key] = p;
+  }
+  return xs_seg_plan_launch(p, stream);
+}
+
+xs_status xs_autotune_segments(const double* d_values, const int64_t* d_offsets, int64_t nseg,
+                               double* d_out, int reps, void* stream, xs_seg_options* best,
+                               float* best_us) {
+  if (reps <= 0 || nseg <= 0) return set_error(XS_ERR_INVALID_VALUE);
+  xs_status st;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  cudaStream_t s = as_stream(stream);
+  std::vector<xs_seg_options> cands;
+  const int blocks[][2] = {{128, 4}, {192, 4}, {256, 4}, {384, 4}, {192, 8}};
+  const int tiles[] = {1 << 16, 1 << 17, 1 << 18};
+  const int shorts[] = {1024, 4096, 16384};
+  for (auto& b : blocks)
+    for (int t : tiles)
+      for (int sm : shorts) {
+        xs_seg_options o{b[0], b[1], t, sm, 0};
+        if ((long long)t > 2040LL * b[0]) continue;
+        cands.push_back(o);
+      }
+  cudaEvent_t e0, e1;
+  XS_TRY_CUDA(cudaEventCreate(&e0));
+  XS_TRY_CUDA(cudaEventCreate(&e1));
+  float bt = 1e30f;
+  xs_seg_options win = cands[0];
+  std::vector<float> ts;
+  for (const auto& o : cands) {
+    xs_seg_plan p = nullptr;
+    st = xs_seg_plan_create(&p, d_values, d_offsets, nseg, d_out, &o, stream);
+    if (st == XS_ERR_NOT_SUPPORTED) continue;
+    if (st != XS_OK) return st;
+    if ((st = xs_seg_plan_launch(p, stream)) != XS_OK) return st;  // warm-up
+    ts.clear();
+    for (int r = 0; r < reps; ++r) {
+      XS_TRY_CUDA(cudaEventRecord(e0, s));
+      if ((st = xs_seg_plan_launch(p, stream)) != XS_OK) return st;
+      XS_TRY_CUDA(cudaEventRecord(e1, s));
+      XS_TRY_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      XS_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      ts.push_back(ms);
+    }
+    xs_seg_plan_destroy(p);
+    std::sort(ts.begin(), ts.end());
+    if (ts[ts.size() / 2] < bt) {
+      bt = ts[ts.size() / 2];
+      win = o;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->tuned_seg = win;
+    ctx->have_tuned_seg = true;
+  }
+  if (best) *best = win;
+  if (best_us) *best_us = bt * 1000.f;
+  return set_error(XS_OK);
+}
+
+}  // extern "C"

@@ -1,0 +1,301 @@
+"""Thin ctypes binding of libxsum.so: the C ABI of include/xsum.h, same names.
+
+Argument marshalling only: every computation happens in the CUDA library.
+Pointer arguments accept plain integers (device or host addresses) or objects
+with ``data_ptr()`` (torch tensors); ``stream`` accepts an integer handle, a
+``torch.cuda.Stream`` or None (the current torch stream when torch is loaded,
+else the legacy default stream). There is no CPU fallback: if the library is
+missing or cannot load, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libxsum.so")
+
+XS_OK = 0
+XS_ERR_INVALID_VALUE = 1
+XS_ERR_INVALID_POINTER = 2
+XS_ERR_OUT_OF_MEMORY = 3
+XS_ERR_CUDA = 4
+XS_ERR_TIMEOUT = 5
+XS_ERR_BUDGET = 6
+XS_ERR_NOT_SUPPORTED = 7
+XS_ERR_NOT_READY = 8
+
+XS_METHOD_AUTO = 0
+XS_METHOD_SMALL = 1
+XS_METHOD_LARGE = 2
+XS_ACC_BYTES = 560
+
+_c_int64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+
+
+class XsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class xs_seg_options(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("unroll", ctypes.c_int), ("tile_elems", ctypes.c_int),
+                ("short_max", ctypes.c_int), ("carry_tiles", ctypes.c_int)]
+
+
+# name: (restype, argtypes)
+_SIGS = {
+    "xs_version": (ctypes.c_char_p, []),
+    "xs_get_last_error": (ctypes.c_int, []),
+    "xs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "xs_sum": (ctypes.c_double, [_vp, _c_int64, _vp]),
+    "xs_sum_ex": (ctypes.c_int, [_vp, _c_int64, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "xs_sum_async": (ctypes.c_int, [_vp, _c_int64, _vp, ctypes.c_int, _vp]),
+    "xs_sum_async_config": (ctypes.c_int, [_vp, _c_int64, _vp, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, _vp]),
+    "xs_list_configs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "xs_sum_host": (ctypes.c_int, [_vp, _c_int64, ctypes.POINTER(ctypes.c_double), _vp]),
+    "xs_inexact_sum_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
+    "xs_autotune_sum": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "xs_sum_segments": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, _vp]),
+    "xs_seg_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, _vp, _c_int64, _vp,
+                                          ctypes.POINTER(xs_seg_options), _vp]),
+    "xs_seg_plan_launch": (ctypes.c_int, [_vp, _vp]),
+    "xs_seg_plan_launch_direct": (ctypes.c_int, [_vp, _vp]),
+    "xs_seg_plan_kernel_launches": (ctypes.c_int, [_vp]),
+    "xs_seg_plan_destroy": (ctypes.c_int, [_vp]),
+    "xs_autotune_segments": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, ctypes.c_int, _vp,
+                                            ctypes.POINTER(xs_seg_options),
+                                            ctypes.POINTER(ctypes.c_float)]),
+    "xs_acc_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp]),
+    "xs_acc_init": (ctypes.c_int, [_vp, _vp]),
+    "xs_acc_add": (ctypes.c_int, [_vp, _vp, _c_int64, _vp]),
+    "xs_acc_merge": (ctypes.c_int, [_vp, _vp, _vp]),
+    "xs_acc_round": (ctypes.c_int, [_vp, _vp, _vp]),
+    "xs_acc_export": (ctypes.c_int, [_vp, _vp, _vp]),
+    "xs_acc_import": (ctypes.c_int, [_vp, _vp, _vp]),
+    "xs_acc_destroy": (ctypes.c_int, [_vp]),
+    "xs_acc_device_state": (_vp, [_vp]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads libxsum.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libxsum.so not built ({p}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "value"):
+        return x.value
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(status: int, where: str) -> None:
+    if status != XS_OK:
+        raise XsError(status, where)
+
+
+def status_string(s: int) -> str:
+    return load().xs_status_string(s).decode()
+
+
+def xs_version() -> str:
+    return load().xs_version().decode()
+
+
+def xs_get_last_error() -> int:
+    return load().xs_get_last_error()
+
+
+def xs_sum(d_values, n: int, stream=None) -> float:
+    return load().xs_sum(_ptr(d_values), n, _stream(stream))
+
+
+def xs_sum_ex(d_values, n: int, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(load().xs_sum_ex(_ptr(d_values), n, _stream(stream), ctypes.byref(out)), "xs_sum_ex")
+    return out.value
+
+
+def xs_sum_async(d_values, n: int, d_out, method: int = XS_METHOD_AUTO, stream=None) -> None:
+    _check(load().xs_sum_async(_ptr(d_values), n, _ptr(d_out), method, _stream(stream)),
+           "xs_sum_async")
+
+
+def xs_sum_async_config(d_values, n: int, d_out, method: int, block: int, unroll: int,
+                        grid: int = 0, stream=None) -> None:
+    _check(load().xs_sum_async_config(_ptr(d_values), n, _ptr(d_out), method, block, unroll, grid,
+                                      _stream(stream)), "xs_sum_async_config")
+
+
+def xs_list_configs() -> list[tuple[int, int, int]]:
+    lib = load()
+    k = lib.xs_list_configs(None, None, None, 0)
+    m = (ctypes.c_int * k)()
+    b = (ctypes.c_int * k)()
+    u = (ctypes.c_int * k)()
+    lib.xs_list_configs(m, b, u, k)
+    return [(m[i], b[i], u[i]) for i in range(k)]
+
+
+def xs_sum_host(h_values, n: int, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(load().xs_sum_host(_ptr(h_values), n, ctypes.byref(out), _stream(stream)), "xs_sum_host")
+    return out.value
+
+
+def xs_inexact_sum_async(d_values, n: int, d_out, stream=None) -> None:
+    _check(load().xs_inexact_sum_async(_ptr(d_values), n, _ptr(d_out), _stream(stream)),
+           "xs_inexact_sum_async")
+
+
+def xs_autotune_sum(d_values, n: int, reps: int = 5, stream=None):
+    m, b, u, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(load().xs_autotune_sum(_ptr(d_values), n, reps, _stream(stream), ctypes.byref(m),
+                                  ctypes.byref(b), ctypes.byref(u), ctypes.byref(t)),
+           "xs_autotune_sum")
+    return {"method": m.value, "block": b.value, "unroll": u.value, "us": t.value}
+
+
+def xs_sum_segments(d_values, d_offsets, nseg: int, d_out, stream=None) -> None:
+    _check(load().xs_sum_segments(_ptr(d_values), _ptr(d_offsets), nseg, _ptr(d_out),
+                                  _stream(stream)), "xs_sum_segments")
+
+
+def _opts(opts) -> xs_seg_options | None:
+    if opts is None:
+        return None
+    if isinstance(opts, xs_seg_options):
+        return opts
+    o = xs_seg_options()
+    for k, v in dict(opts).items():
+        setattr(o, k, int(v))
+    return o
+
+
+def xs_seg_plan_create(d_values, d_offsets, nseg: int, d_out, opts=None, stream=None) -> int:
+    h = _vp()
+    o = _opts(opts)
+    _check(load().xs_seg_plan_create(ctypes.byref(h), _ptr(d_values), _ptr(d_offsets), nseg,
+                                     _ptr(d_out), ctypes.byref(o) if o is not None else None,
+                                     _stream(stream)), "xs_seg_plan_create")
+    return h.value
+
+
+def xs_seg_plan_launch(plan: int, stream=None) -> None:
+    _check(load().xs_seg_plan_launch(plan, _stream(stream)), "xs_seg_plan_launch")
+
+
+def xs_seg_plan_launch_direct(plan: int, stream=None) -> None:
+    _check(load().xs_seg_plan_launch_direct(plan, _stream(stream)), "xs_seg_plan_launch_direct")
+
+
+def xs_seg_plan_kernel_launches(plan: int) -> int:
+    return load().xs_seg_plan_kernel_launches(plan)
+
+
+def xs_seg_plan_destroy(plan: int) -> None:
+    _check(load().xs_seg_plan_destroy(plan), "xs_seg_plan_destroy")
+
+
+def xs_autotune_segments(d_values, d_offsets, nseg: int, d_out, reps: int = 3, stream=None):
+    o = xs_seg_options()
+    t = ctypes.c_float()
+    _check(load().xs_autotune_segments(_ptr(d_values), _ptr(d_offsets), nseg, _ptr(d_out), reps,
+                                       _stream(stream), ctypes.byref(o), ctypes.byref(t)),
+           "xs_autotune_segments")
+    return {f: getattr(o, f) for f, _ in xs_seg_options._fields_} | {"us": t.value}
+
+
+def xs_acc_create(stream=None) -> int:
+    h = _vp()
+    _check(load().xs_acc_create(ctypes.byref(h), _stream(stream)), "xs_acc_create")
+    return h.value
+
+
+def xs_acc_init(h: int, stream=None) -> None:
+    _check(load().xs_acc_init(h, _stream(stream)), "xs_acc_init")
+
+
+def xs_acc_add(h: int, d_values, n: int, stream=None) -> None:
+    _check(load().xs_acc_add(h, _ptr(d_values), n, _stream(stream)), "xs_acc_add")
+
+
+def xs_acc_merge(dst: int, src: int, stream=None) -> None:
+    _check(load().xs_acc_merge(dst, src, _stream(stream)), "xs_acc_merge")
+
+
+def xs_acc_round(h: int, d_out, stream=None) -> None:
+    _check(load().xs_acc_round(h, _ptr(d_out), _stream(stream)), "xs_acc_round")
+
+
+def xs_acc_export(h: int, stream=None) -> bytes:
+    buf = ctypes.create_string_buffer(XS_ACC_BYTES)
+    _check(load().xs_acc_export(h, buf, _stream(stream)), "xs_acc_export")
+    return buf.raw
+
+
+def xs_acc_import(h: int, state: bytes, stream=None) -> None:
+    if len(state) != XS_ACC_BYTES:
+        raise ValueError("state must be XS_ACC_BYTES long")
+    buf = ctypes.create_string_buffer(state, XS_ACC_BYTES)
+    _check(load().xs_acc_import(h, buf, _stream(stream)), "xs_acc_import")
+
+
+def xs_acc_destroy(h: int) -> None:
+    _check(load().xs_acc_destroy(h), "xs_acc_destroy")
+
+
+def xs_acc_device_state(h: int) -> int:
+    return load().xs_acc_device_state(h)
+
+
+def acc_state_chunks(state: bytes) -> list[int]:
+    """The 67 signed chunks of an exported state (little-endian int64)."""
+    return list(struct.unpack("<67q", state[:536]))

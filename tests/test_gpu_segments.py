@@ -1,0 +1,141 @@
+"""Batched segmented exact sums (CSR) against the oracle, per segment, bit for bit."""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import c_oracle
+from paper_1505_05571_gb300 import xsum
+from tests.gpu_util import bits_of, to_device
+from workloads import devgen
+
+pytestmark = pytest.mark.gpu
+
+OPTS = [
+    None,
+    {"block": 128, "unroll": 4, "tile_elems": 1 << 12, "short_max": 64},
+    {"block": 192, "unroll": 4, "tile_elems": 1 << 16, "short_max": 1024},
+    {"block": 256, "unroll": 4, "tile_elems": 1 << 13, "short_max": 4096},
+    {"block": 384, "unroll": 4, "tile_elems": 1 << 18, "short_max": 16384},
+    {"block": 192, "unroll": 8, "tile_elems": 3000, "short_max": 0},
+]
+
+
+def mixed_lengths(seed, nseg):
+    rng = np.random.default_rng(seed)
+    lengths = W.cfg3_lengths(seed, nseg, 200_000)
+    special = np.array([0, 1, 2, 3, 31, 32, 33, 64, 65, 4096, 4097, 8191, 8193, 12289], dtype=np.int64)
+    pos = rng.integers(0, nseg, special.size)
+    lengths[pos] = special
+    return lengths
+
+
+def run_plan(vals_dev, off_dev, nseg, opts, graph=True):
+    out = torch.full((nseg,), float("nan"), dtype=torch.float64, device="cuda")
+    p = xsum.xs_seg_plan_create(vals_dev, off_dev, nseg, out, opts)
+    try:
+        for _ in range(2):  # repeated launches reuse the self-resetting work space
+            out.fill_(float("nan"))
+            if graph:
+                xsum.xs_seg_plan_launch(p)
+            else:
+                xsum.xs_seg_plan_launch_direct(p)
+        torch.cuda.synchronize()
+    finally:
+        xsum.xs_seg_plan_destroy(p)
+    return bits_of(out)
+
+
+@pytest.mark.parametrize("opts", OPTS, ids=[str(o) for o in OPTS])
+def test_segments_mixed(opts):
+    nseg = 3000
+    lengths = mixed_lengths(1, nseg)
+    off = W.cfg3_offsets(lengths)
+    vals = W.cfg2a_paired(5, 0, int(off[-1]))
+    specials = np.array([0x7FF0000000000000, 0xFFF0000000000000, 0x7FF8000000000077,
+                         0x8000000000000000], dtype=np.uint64)
+    rng = np.random.default_rng(2)
+    sel = rng.integers(0, vals.size, 40)
+    vals[sel] = specials[rng.integers(0, 4, sel.size)]
+    # a segment of only -0 and one of +0, -0
+    z0 = int(np.argmax(lengths == 3))
+    vals[off[z0]:off[z0 + 1]] = 0x8000000000000000
+    expect = c_oracle.segment_sums_bits(vals, off)
+    vd = to_device(vals)
+    od = torch.from_numpy(off).cuda()
+    got = run_plan(vd, od, nseg, opts)
+    bad = np.nonzero(got != expect)[0]
+    assert bad.size == 0, [(int(k), int(lengths[k]), hex(got[k]), hex(expect[k])) for k in bad[:5]]
+    got2 = run_plan(vd, od, nseg, opts, graph=False)
+    assert np.array_equal(got2, expect)
+
+
+def test_segments_unaligned_values_and_convenience_api():
+    nseg = 500
+    lengths = mixed_lengths(3, nseg)
+    off = W.cfg3_offsets(lengths)
+    vals = W.cfg3_values(3, 0, int(off[-1]))
+    vd = to_device(vals, misalign=1)
+    od = torch.from_numpy(off).cuda()
+    out = torch.empty(nseg, dtype=torch.float64, device="cuda")
+    xsum.xs_sum_segments(vd, od, nseg, out)
+    xsum.xs_sum_segments(vd, od, nseg, out)  # cached plan, graph replay
+    assert np.array_equal(bits_of(out), c_oracle.segment_sums_bits(vals, off))
+
+
+def test_segments_repeats_closed_form():
+    """Long segments of one repeated value: fl(N v) per segment, across tiles."""
+    vs = [0.1, 1.0 - 2.0 ** -53, 3 * 5e-324, -0.7]
+    Ns = [1, 2, 4095, 4097, 300_001]
+    lengths, vals, expect = [], [], []
+    for v in vs:
+        for N in Ns:
+            lengths.append(N)
+            vals.append(np.full(N, v))
+            expect.append(np.array([v * N]).view(np.uint64)[0])
+    off = W.cfg3_offsets(np.array(lengths, dtype=np.int64))
+    vd = torch.from_numpy(np.concatenate(vals)).cuda()
+    od = torch.from_numpy(off).cuda()
+    got = run_plan(vd, od, len(lengths), {"block": 192, "unroll": 4, "tile_elems": 8192,
+                                          "short_max": 1024})
+    assert np.array_equal(got, np.array(expect, dtype=np.uint64))
+
+
+def test_segments_autotune_then_default():
+    nseg = 2000
+    lengths = mixed_lengths(4, nseg)
+    off = W.cfg3_offsets(lengths)
+    vals = W.cfg3_values(4, 0, int(off[-1]))
+    vd, od = to_device(vals), torch.from_numpy(off).cuda()
+    out = torch.empty(nseg, dtype=torch.float64, device="cuda")
+    best = xsum.xs_autotune_segments(vd, od, nseg, out, reps=2)
+    assert best["us"] > 0
+    got = run_plan(vd, od, nseg, None)
+    assert np.array_equal(got, c_oracle.segment_sums_bits(vals, off))
+
+
+def test_full_cfg3_sampled():
+    """100,000 segments, lengths log-uniform in [1, 1e6] (about 7.2e9 values,
+    58 GB generated in HBM); sampled segments checked against the oracle."""
+    nseg = 100_000
+    lengths = W.cfg3_lengths(0, nseg, 10 ** 6)
+    off = W.cfg3_offsets(lengths)
+    total = int(off[-1])
+    free, _ = torch.cuda.mem_get_info()
+    if total * 8 > free - (8 << 30):
+        pytest.skip(f"needs {total * 8 / 2**30:.1f} GiB free, have {free / 2**30:.1f}")
+    vals = torch.empty(total, dtype=torch.int64, device="cuda")
+    devgen.band(vals, 0, 0, -30, 30)
+    od = torch.from_numpy(off).cuda()
+    out = torch.empty(nseg, dtype=torch.float64, device="cuda")
+    xsum.xs_sum_segments(vals.view(torch.float64), od, nseg, out)
+    got = bits_of(out)
+    del vals
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(0)
+    sample = np.unique(np.concatenate([rng.integers(0, nseg, 120), np.argsort(lengths)[-8:],
+                                       np.argsort(lengths)[:8]]))
+    for s in sample:
+        seg = W.cfg3_values(0, int(off[s]), int(lengths[s]))
+        assert got[s] == c_oracle.sum_bits(seg), int(s)

@@ -116,6 +116,14 @@ def full_range_bits(u: np.ndarray, v: np.ndarray, emax_excl: int = 2047) -> np.n
     return (u & np.uint64(SIGN_BIT)) | (e << np.uint64(52)) | (u & np.uint64(MANT_MASK))
 
 
+def affine_constants(seed: int, n_log2: int) -> tuple[int, int]:
+    """(A^{-1} mod 2**n_log2, B) of the bijection pi(k) = (A*k + B) mod 2**n_log2, A odd."""
+    n = 1 << n_log2
+    a = (mix64_int(stream_key(seed, "perm")) | 1) & (n - 1)
+    b = mix64_int(stream_key(seed, "perm") + 1) & (n - 1)
+    return pow(a, -1, n), b
+
+
 def affine_perm_inverse(seed: int, n_log2: int, i: np.ndarray) -> np.ndarray:
     """Inverse of the bijection pi(k) = (A*k + B) mod 2**n_log2 (A odd).
 
@@ -123,9 +131,7 @@ def affine_perm_inverse(seed: int, n_log2: int, i: np.ndarray) -> np.ndarray:
     permutation: X[i] = base[pi^{-1}(i)].
     """
     n = 1 << n_log2
-    a = (mix64_int(stream_key(seed, "perm")) | 1) & (n - 1)
-    b = mix64_int(stream_key(seed, "perm") + 1) & (n - 1)
-    a_inv = pow(a, -1, n)
+    a_inv, b = affine_constants(seed, n_log2)
     i = np.asarray(i, dtype=np.uint64)
     with np.errstate(over="ignore"):
         return ((i - np.uint64(b)) * np.uint64(a_inv)) & np.uint64(n - 1)
