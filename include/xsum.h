@@ -104,6 +104,11 @@ xs_status xs_sum_async(const double* d_values, int64_t n, double* d_out, int met
 xs_status xs_sum_async_config(const double* d_values, int64_t n, double* d_out, int method,
                               int block, int unroll, int grid, void* stream);
 
+/* Launch shape that XS_METHOD_AUTO uses for n elements on the current device:
+ * the autotuned choice for n's size class if there is one, else the built-in
+ * default. */
+xs_status xs_default_shape(int64_t n, int* method, int* block, int* unroll);
+
 /* Number of compiled launch shapes, and shape k as (method, block, unroll). */
 int xs_list_configs(int* methods, int* blocks, int* unrolls, int capacity);
 

@@ -337,7 +337,10 @@ const KernelEntry kKernels[] = {
     {XS_METHOD_SMALL, 128, 8, k_sum_small<128, 8>, small_smem<128>()},
     {XS_METHOD_SMALL, 256, 4, k_sum_small<256, 4>, small_smem<256>()},
     {XS_METHOD_SMALL, 256, 8, k_sum_small<256, 8>, small_smem<256>()},
+    {XS_METHOD_SMALL, 192, 4, k_sum_small<192, 4>, small_smem<192>()},
+    {XS_METHOD_SMALL, 192, 8, k_sum_small<192, 8>, small_smem<192>()},
     {XS_METHOD_SMALL, 384, 4, k_sum_small<384, 4>, small_smem<384>()},
+    {XS_METHOD_SMALL, 416, 4, k_sum_small<416, 4>, small_smem<416>()},
     {XS_METHOD_SMALL, 384, 8, k_sum_small<384, 8>, small_smem<384>()},
     {XS_METHOD_LARGE, 256, 4, k_sum_large<256, 4>, sizeof(LargeSmem)},
     {XS_METHOD_LARGE, 256, 8, k_sum_large<256, 8>, sizeof(LargeSmem)},
@@ -461,8 +464,9 @@ Workspace* workspace(DeviceCtx* ctx, cudaStream_t s, xs_status* st) {
 SumShape default_shape(DeviceCtx* ctx, int64_t n) {
   auto it = ctx->tuned_sum.find(size_class(n));
   if (it != ctx->tuned_sum.end()) return it->second;
+  // measured on GB300: per-thread small superaccumulators win at every size
   if (n < (int64_t(1) << 20)) return SumShape{XS_METHOD_SMALL, 128, 4};
-  return SumShape{XS_METHOD_LARGE, 256, 8};
+  return SumShape{XS_METHOD_SMALL, 384, 4};
 }
 
 xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState* target,
@@ -510,6 +514,18 @@ const char* xs_status_string(xs_status s) {
     case XS_ERR_NOT_READY: return "not ready";
   }
   return "unknown status";
+}
+
+xs_status xs_default_shape(int64_t n, int* method, int* block, int* unroll) {
+  if (n < 0) return set_error(XS_ERR_INVALID_VALUE);
+  xs_status st;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  const SumShape sh = default_shape(ctx, n);
+  if (method) *method = sh.method;
+  if (block) *block = sh.block;
+  if (unroll) *unroll = sh.unroll;
+  return set_error(XS_OK);
 }
 
 int xs_list_configs(int* methods, int* blocks, int* unrolls, int capacity) {

@@ -108,14 +108,42 @@ __device__ __forceinline__ void sacc_add(long long* __restrict__ a, int stride,
   c[stride] += (vhi ^ s) - s;
 }
 
+// Add one NORMAL finite term (1 <= e <= 2046) -- the common case, kept short
+// because the small-superaccumulator kernel is bound by integer issue:
+//   t = sign:exponent, i = e >> 5, 2^l from a wrap-mode funnel shift,
+//   M << l as two 32x32->64 multiplies by 2^l (FMA pipe instead of shifts),
+//   conditional negation by XOR with the sign mask plus the sign bit, folded
+//   into the three-input adds of the two chunk updates.
+__device__ __forceinline__ void sacc_add_normal(long long* __restrict__ a, int stride,
+                                                unsigned lo, unsigned hi) {
+  const unsigned t = hi >> 20;                        // sign and biased exponent
+  const unsigned i = (t & 0x7FFu) >> kLowExpBits;     // chunk index, 0..63
+  const unsigned pw = __funnelshift_l(0u, 1u, t);     // 2^(t & 31) = 2^l
+  const unsigned mh = (hi & 0xFFFFFu) | 0x100000u;    // high 21 bits of M
+  const unsigned long long P = (unsigned long long)lo * pw;            // lo << l
+  const unsigned long long Q = (unsigned long long)mh * pw + (P >> 32);  // (M << l) >> 32
+  const unsigned s = (unsigned)((int)hi >> 31);       // 0 or 0xFFFFFFFF
+  const unsigned long long s64 = ((unsigned long long)s << 32) | s;
+  const unsigned long long s1 = s & 1u;
+  const unsigned long long vlo = ((unsigned long long)s << 32) | ((unsigned)P ^ s);
+  long long* c = a + (int)i * stride;
+  c[0] += (long long)(vlo + s1);
+  c[stride] += (long long)((Q ^ s64) + s1);
+}
+
 // Per-thread state of the small-superaccumulator path: the chunks plus the
 // Inf/NaN record and what decides the sign of an exact zero.
 struct SmallThread {
   long long* acc;  // this thread's chunks, stride BLOCK
-  unsigned and_hi = 0x80000000u, or_hi = 0x80000000u, or_lo = 0u;
+  unsigned notnegz = 0u;  // saw a term other than -0
   unsigned sflags = 0u;
   unsigned long long nkey = 0ull;
 
+  __device__ __forceinline__ void reset() {
+    notnegz = 0u;
+    sflags = 0u;
+    nkey = 0ull;
+  }
   __device__ __forceinline__ void special(unsigned long long b) {
     if (b & kMantMask) {
       const unsigned long long k = nan_key_of(b);
@@ -124,38 +152,34 @@ struct SmallThread {
       sflags |= (b >> 63) ? kFlagNegInf : kFlagPosInf;
     }
   }
+  // Any term: zeros, subnormals and Inf/NaN included.
   template <int BLOCK>
   __device__ __forceinline__ void one(unsigned long long b) {
     const unsigned lo = (unsigned)b, hi = (unsigned)(b >> 32);
-    and_hi &= hi;
-    or_hi |= hi;
-    or_lo |= lo;
+    notnegz |= (b != kNegZero) ? 1u : 0u;
     if (((hi >> 20) & 0x7FFu) == 0x7FFu) {
       special(b);
     } else {
       sacc_add(acc, BLOCK, lo, hi);
     }
   }
+  __device__ __forceinline__ static bool is_normal(unsigned hi) {
+    return ((hi >> 20) & 0x7FFu) - 1u < 0x7FEu;
+  }
   template <int BLOCK>
   __device__ __forceinline__ void two(unsigned long long a, unsigned long long b) {
-    const unsigned alo = (unsigned)a, ahi = (unsigned)(a >> 32);
-    const unsigned blo = (unsigned)b, bhi = (unsigned)(b >> 32);
-    and_hi &= ahi & bhi;
-    or_hi |= ahi | bhi;
-    or_lo |= alo | blo;
-    const bool sa = ((ahi >> 20) & 0x7FFu) == 0x7FFu;
-    const bool sb = ((bhi >> 20) & 0x7FFu) == 0x7FFu;
-    if (__builtin_expect(sa || sb, 0)) {
-      if (sa) special(a); else sacc_add(acc, BLOCK, alo, ahi);
-      if (sb) special(b); else sacc_add(acc, BLOCK, blo, bhi);
+    const unsigned ahi = (unsigned)(a >> 32), bhi = (unsigned)(b >> 32);
+    if (__builtin_expect(is_normal(ahi) && is_normal(bhi), 1)) {
+      notnegz = 1u;
+      sacc_add_normal(acc, BLOCK, (unsigned)a, ahi);
+      sacc_add_normal(acc, BLOCK, (unsigned)b, bhi);
     } else {
-      sacc_add(acc, BLOCK, alo, ahi);
-      sacc_add(acc, BLOCK, blo, bhi);
+      one<BLOCK>(a);
+      one<BLOCK>(b);
     }
   }
   __device__ __forceinline__ unsigned flags() const {
-    return sflags | ((and_hi != 0x80000000u || or_hi != 0x80000000u || or_lo != 0u)
-                         ? kFlagNotNegZero : 0u);
+    return sflags | (notnegz ? kFlagNotNegZero : 0u);
   }
 };
 

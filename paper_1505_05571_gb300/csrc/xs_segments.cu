@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     const long long lo = seg_lo + (t - first_tile) * a.tile_elems;
     const long long hi = min(lo + a.tile_elems, seg_hi);
     for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
-    T.and_hi = 0x80000000u; T.or_hi = 0x80000000u; T.or_lo = 0u; T.sflags = 0u; T.nkey = 0ull;
+    T.reset();
     accumulate_range<BLOCK, UNROLL>(T, a.x, lo, hi, tid, BLOCK);
     __syncthreads();
     unsigned f = __reduce_or_sync(kFull, T.flags());
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
       }
     }
     for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
-    T.and_hi = 0x80000000u; T.or_hi = 0x80000000u; T.or_lo = 0u; T.sflags = 0u; T.nkey = 0ull;
+    T.reset();
     accumulate_range<BLOCK, 2>(T, a.x, lo, hi, lane, 32);
     __syncwarp();
     // lane L gathers chunks L, L+32, L+64 of the warp's 32 accumulators, split

@@ -58,6 +58,8 @@ _SIGS = {
     "xs_sum_async_config": (ctypes.c_int, [_vp, _c_int64, _vp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int, _vp]),
     "xs_list_configs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "xs_default_shape": (ctypes.c_int, [_c_int64, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "xs_sum_host": (ctypes.c_int, [_vp, _c_int64, ctypes.POINTER(ctypes.c_double), _vp]),
     "xs_inexact_sum_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_autotune_sum": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp,
@@ -172,6 +174,13 @@ def xs_sum_async_config(d_values, n: int, d_out, method: int, block: int, unroll
                         grid: int = 0, stream=None) -> None:
     _check(load().xs_sum_async_config(_ptr(d_values), n, _ptr(d_out), method, block, unroll, grid,
                                       _stream(stream)), "xs_sum_async_config")
+
+
+def xs_default_shape(n: int) -> dict:
+    m, b, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().xs_default_shape(n, ctypes.byref(m), ctypes.byref(b), ctypes.byref(u)),
+           "xs_default_shape")
+    return {"method": m.value, "block": b.value, "unroll": u.value}
 
 
 def xs_list_configs() -> list[tuple[int, int, int]]:
