@@ -28,6 +28,7 @@ struct SumArgs {
   double* out;     // mode 0: result
   int mode;        // 0: round into out and reset g; 1: normalise g in place
   int carry_tiles; // small kernel: tiles between per-thread carry propagations
+  int prefetch;    // tiles of this block prefetched into L2 ahead of use (0 = off)
 };
 
 // Ticket epilogue: the last block to arrive finishes the sum.
@@ -86,6 +87,15 @@ __device__ __forceinline__ Split split_input(const double* x, long long n) {
   return s;
 }
 
+// L2 prefetch of tile t (clamped to the input).
+template <int BLOCK, int UNROLL>
+__device__ __forceinline__ void prefetch_tile(const Split& sp, long long t, long long ntiles) {
+  if (t >= ntiles) return;
+  const long long first = t * (long long)(BLOCK * UNROLL);
+  const long long cnt = min((long long)(BLOCK * UNROLL), sp.npairs - first);
+  prefetch_l2(sp.xv + first, (unsigned)(cnt * 16));
+}
+
 template <int BLOCK, int UNROLL>
 __device__ __forceinline__ void load_tile(const Split& sp, long long t, int tid, ulonglong2* buf) {
   const long long base = t * (long long)(BLOCK * UNROLL) + tid;
@@ -117,6 +127,14 @@ __device__ __forceinline__ void block_small_to_global(const long long* sm, const
   }
 }
 
+// Full tile t: no bounds checks.
+template <int BLOCK, int UNROLL>
+__device__ __forceinline__ void load_full(const Split& sp, long long t, int tid, ulonglong2* buf) {
+  const ulonglong2* p = sp.xv + t * (long long)(BLOCK * UNROLL) + tid;
+#pragma unroll
+  for (int u = 0; u < UNROLL; ++u) buf[u] = ld_stream(p + u * BLOCK);
+}
+
 template <int BLOCK, int UNROLL>
 __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   extern __shared__ __align__(16) long long smem_small[];
@@ -131,23 +149,41 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
     if (sp.head) T.one<BLOCK>(xb[0]);
     if (sp.tail) T.one<BLOCK>(xb[a.n - 1]);
   }
-  const long long ntiles = (sp.npairs + (long long)(BLOCK * UNROLL) - 1) / (BLOCK * UNROLL);
+  constexpr long long TP = (long long)BLOCK * UNROLL;
+  const long long ntiles = (sp.npairs + TP - 1) / TP;
+  const long long nfull = sp.npairs / TP;  // tiles without a ragged end
+  const long long G = gridDim.x;
   long long t = blockIdx.x;
-  ulonglong2 cur[UNROLL];
-  if (t < ntiles) load_tile<BLOCK, UNROLL>(sp, t, tid, cur);
+  if (tid == 0)
+    for (int k = 1; k <= a.prefetch; ++k) prefetch_tile<BLOCK, UNROLL>(sp, t + k * G, ntiles);
   int since = 0;
-  for (; t < ntiles; t += gridDim.x) {
-    ulonglong2 nxt[UNROLL];
-    const long long tn = t + gridDim.x;
-    if (tn < ntiles) load_tile<BLOCK, UNROLL>(sp, tn, tid, nxt);
-#pragma unroll
-    for (int u = 0; u < UNROLL; ++u) T.two<BLOCK>(cur[u].x, cur[u].y);
+  auto tick = [&]() {
     if (++since >= a.carry_tiles) {
       sacc_propagate(T.acc, BLOCK);
       since = 0;
     }
-#pragma unroll
-    for (int u = 0; u < UNROLL; ++u) cur[u] = nxt[u];
+  };
+  // Full tiles, two register buffers used in turn: the loads of the next
+  // tile are in flight while the current one is added.
+  ulonglong2 A[UNROLL], B[UNROLL];
+  if (t < nfull) load_full<BLOCK, UNROLL>(sp, t, tid, A);
+  while (t < nfull) {
+    if (tid == 0 && a.prefetch > 0) prefetch_tile<BLOCK, UNROLL>(sp, t + (a.prefetch + 1) * G, ntiles);
+    if (t + G < nfull) load_full<BLOCK, UNROLL>(sp, t + G, tid, B);
+    T.group<BLOCK, UNROLL>(A);
+    tick();
+    t += G;
+    if (t >= nfull) break;
+    if (tid == 0 && a.prefetch > 0) prefetch_tile<BLOCK, UNROLL>(sp, t + (a.prefetch + 1) * G, ntiles);
+    if (t + G < nfull) load_full<BLOCK, UNROLL>(sp, t + G, tid, A);
+    T.group<BLOCK, UNROLL>(B);
+    tick();
+    t += G;
+  }
+  // The ragged last tile (padded with -0, which adds nothing).
+  if (t == nfull && nfull < ntiles) {
+    load_tile<BLOCK, UNROLL>(sp, t, tid, A);
+    T.group<BLOCK, UNROLL>(A);
   }
   __syncthreads();
   unsigned f = T.flags();
@@ -348,6 +384,7 @@ const KernelEntry kKernels[] = {
 };
 constexpr int kNumKernels = sizeof(kKernels) / sizeof(kKernels[0]);
 
+int g_prefetch_tiles = 3;  // L2 prefetch distance of the single-array kernels, in tiles
 std::mutex g_ctx_mu;
 std::map<int, DeviceCtx*> g_ctx;
 
@@ -486,6 +523,7 @@ xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState
   a.out = d_out;
   a.mode = mode;
   a.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * K.unroll));
+  a.prefetch = g_prefetch_tiles;
   K.fn<<<(unsigned)g, K.block, K.smem, s>>>(a);
   XS_TRY_CUDA(cudaGetLastError());
   return XS_OK;
@@ -525,6 +563,12 @@ xs_status xs_default_shape(int64_t n, int* method, int* block, int* unroll) {
   if (method) *method = sh.method;
   if (block) *block = sh.block;
   if (unroll) *unroll = sh.unroll;
+  return set_error(XS_OK);
+}
+
+xs_status xs_set_prefetch_tiles(int tiles) {
+  if (tiles < 0 || tiles > 64) return set_error(XS_ERR_INVALID_VALUE);
+  g_prefetch_tiles = tiles;
   return set_error(XS_OK);
 }
 

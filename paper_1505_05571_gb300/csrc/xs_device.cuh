@@ -81,6 +81,14 @@ __device__ __forceinline__ unsigned long long ld_stream1(const unsigned long lon
   return v;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (TMA engine, no completion to wait
+// for). p must be 16-byte aligned and bytes a multiple of 16; callers clamp the
+// range to their input. Keeps HBM busy beyond what the threads' own loads put
+// in flight.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // --------------------------------------------------------------------------
 // Small superaccumulator, one per thread, chunks strided by `stride` longs.
 // --------------------------------------------------------------------------
@@ -108,27 +116,27 @@ __device__ __forceinline__ void sacc_add(long long* __restrict__ a, int stride,
   c[stride] += (vhi ^ s) - s;
 }
 
-// Add one NORMAL finite term (1 <= e <= 2046) -- the common case, kept short
-// because the small-superaccumulator kernel is bound by integer issue:
-//   t = sign:exponent, i = e >> 5, 2^l from a wrap-mode funnel shift,
+// Add one NORMAL finite term (1 <= e <= 2046, e = its biased exponent) -- the
+// common case, kept short because the small-superaccumulator kernel is bound
+// by instruction issue:
+//   2^l from a wrap-mode funnel shift of e (l = e & 31),
 //   M << l as two 32x32->64 multiplies by 2^l (FMA pipe instead of shifts),
-//   conditional negation by XOR with the sign mask plus the sign bit, folded
-//   into the three-input adds of the two chunk updates.
-__device__ __forceinline__ void sacc_add_normal(long long* __restrict__ a, int stride,
-                                                unsigned lo, unsigned hi) {
-  const unsigned t = hi >> 20;                        // sign and biased exponent
-  const unsigned i = (t & 0x7FFu) >> kLowExpBits;     // chunk index, 0..63
-  const unsigned pw = __funnelshift_l(0u, 1u, t);     // 2^(t & 31) = 2^l
+//   conditional negation as XOR with the sign mask plus the sign bit, which
+//   fuses into the three-input adds of the two chunk updates.
+template <int STRIDE>
+__device__ __forceinline__ void sacc_add_normal(long long* __restrict__ a, unsigned lo,
+                                                unsigned hi, unsigned e) {
+  const unsigned pw = __funnelshift_l(0u, 1u, e);     // 2^(e & 31)
   const unsigned mh = (hi & 0xFFFFFu) | 0x100000u;    // high 21 bits of M
-  const unsigned long long P = (unsigned long long)lo * pw;            // lo << l
+  const unsigned long long P = (unsigned long long)lo * pw;              // lo << l
   const unsigned long long Q = (unsigned long long)mh * pw + (P >> 32);  // (M << l) >> 32
   const unsigned s = (unsigned)((int)hi >> 31);       // 0 or 0xFFFFFFFF
-  const unsigned long long s64 = ((unsigned long long)s << 32) | s;
-  const unsigned long long s1 = s & 1u;
-  const unsigned long long vlo = ((unsigned long long)s << 32) | ((unsigned)P ^ s);
-  long long* c = a + (int)i * stride;
-  c[0] += (long long)(vlo + s1);
-  c[stride] += (long long)((Q ^ s64) + s1);
+  const unsigned s1 = hi >> 31;                       // 0 or 1
+  long long* c = a + (int)(e >> kLowExpBits) * STRIDE;
+  const unsigned long long x0 = ((unsigned long long)s << 32) | ((unsigned)P ^ s);
+  const unsigned long long x1 = Q ^ (((unsigned long long)s << 32) | s);
+  c[0] = (long long)((unsigned long long)c[0] + x0 + s1);
+  c[STRIDE] = (long long)((unsigned long long)c[STRIDE] + x1 + s1);
 }
 
 // Per-thread state of the small-superaccumulator path: the chunks plus the
@@ -163,19 +171,32 @@ struct SmallThread {
       sacc_add(acc, BLOCK, lo, hi);
     }
   }
-  __device__ __forceinline__ static bool is_normal(unsigned hi) {
-    return ((hi >> 20) & 0x7FFu) - 1u < 0x7FEu;
-  }
-  template <int BLOCK>
-  __device__ __forceinline__ void two(unsigned long long a, unsigned long long b) {
-    const unsigned ahi = (unsigned)(a >> 32), bhi = (unsigned)(b >> 32);
-    if (__builtin_expect(is_normal(ahi) && is_normal(bhi), 1)) {
+  // A group of U 16-byte vectors (2U terms): one test decides whether every
+  // term is normal (then the short path), else each term takes the general one.
+  template <int BLOCK, int U>
+  __device__ __forceinline__ void group(const ulonglong2* v) {
+    unsigned e[2 * U];
+    unsigned mx = 0u;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      e[2 * k] = ((unsigned)(v[k].x >> 32) >> 20) & 0x7FFu;
+      e[2 * k + 1] = ((unsigned)(v[k].y >> 32) >> 20) & 0x7FFu;
+      mx = max(mx, e[2 * k] - 1u);  // e == 0 wraps to the top: not normal
+      mx = max(mx, e[2 * k + 1] - 1u);
+    }
+    if (__builtin_expect(mx < 0x7FEu, 1)) {
       notnegz = 1u;
-      sacc_add_normal(acc, BLOCK, (unsigned)a, ahi);
-      sacc_add_normal(acc, BLOCK, (unsigned)b, bhi);
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        sacc_add_normal<BLOCK>(acc, (unsigned)v[k].x, (unsigned)(v[k].x >> 32), e[2 * k]);
+        sacc_add_normal<BLOCK>(acc, (unsigned)v[k].y, (unsigned)(v[k].y >> 32), e[2 * k + 1]);
+      }
     } else {
-      one<BLOCK>(a);
-      one<BLOCK>(b);
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        one<BLOCK>(v[k].x);
+        one<BLOCK>(v[k].y);
+      }
     }
   }
   __device__ __forceinline__ unsigned flags() const {

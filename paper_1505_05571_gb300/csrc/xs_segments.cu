@@ -148,8 +148,7 @@ __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x
       const long long k = q + step + (long long)u * nthr;
       nxt[u] = k < npairs ? ld_stream(xv + k) : make_ulonglong2(kNegZero, kNegZero);
     }
-#pragma unroll
-    for (int u = 0; u < UNROLL; ++u) T.two<BLOCK>(cur[u].x, cur[u].y);
+    T.group<BLOCK, UNROLL>(cur);
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) cur[u] = nxt[u];
   }

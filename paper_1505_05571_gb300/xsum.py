@@ -58,6 +58,7 @@ _SIGS = {
     "xs_sum_async_config": (ctypes.c_int, [_vp, _c_int64, _vp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int, _vp]),
     "xs_list_configs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "xs_set_prefetch_tiles": (ctypes.c_int, [ctypes.c_int]),
     "xs_default_shape": (ctypes.c_int, [_c_int64, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "xs_sum_host": (ctypes.c_int, [_vp, _c_int64, ctypes.POINTER(ctypes.c_double), _vp]),
@@ -181,6 +182,10 @@ def xs_default_shape(n: int) -> dict:
     _check(load().xs_default_shape(n, ctypes.byref(m), ctypes.byref(b), ctypes.byref(u)),
            "xs_default_shape")
     return {"method": m.value, "block": b.value, "unroll": u.value}
+
+
+def xs_set_prefetch_tiles(tiles: int) -> None:
+    _check(load().xs_set_prefetch_tiles(tiles), "xs_set_prefetch_tiles")
 
 
 def xs_list_configs() -> list[tuple[int, int, int]]:
