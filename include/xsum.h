@@ -132,6 +132,39 @@ xs_status xs_inexact_sum_async(const double* d_values, int64_t n, double* d_out,
 xs_status xs_autotune_sum(const double* d_values, int64_t n, int reps, void* stream,
                           int* best_method, int* best_block, int* best_unroll, float* best_us);
 
+/* Largest n that xs_sum_noalloc accepts: 2^45 terms, the count that the
+ * 67-chunk accumulator is guaranteed to hold without overflow. */
+#define XS_NOALLOC_MAX_TERMS (((int64_t)1) << 45)
+
+/* Exact sum for callers that cannot allocate device memory. The paper has no
+ * counterpart: it is a packaging of the single-array sum for such callers.
+ *
+ * Every other entry point may call cudaMalloc on first use (a per-stream work
+ * space). Some callers must not let a library do that: code inside a host
+ * application or framework that owns all device memory through its own pool
+ * and budget (a hidden cudaMalloc escapes its accounting, and cudaFree
+ * synchronizes the whole device), latency-bound loops that cannot afford an
+ * allocation's unpredictable cost, and processes whose device memory is
+ * already full. This entry point performs no cudaMalloc, cudaFree,
+ * cudaMallocHost or other allocating call (torch's allocator included).
+ *
+ * Its only scratch is one 560-byte accumulator per device, a static device
+ * array inside the library that every GPU which loads the library holds until
+ * the process exits. The caller passes the input d_values[0..n) and the
+ * device result slot *d_out, as for xs_sum_async; the call is asynchronous on
+ * `stream`. Each call first clears the accumulator (cudaMemsetAsync), then
+ * launches the sum, which leaves it cleared again.
+ *
+ * - The first call on a device looks up that device's address of the
+ *   accumulator (with the device current); make that first call before any
+ *   stream capture on that device.
+ * - Every call on a device shares the one accumulator: calls that overlap on
+ *   the GPU (different streams, or different host threads without ordering)
+ *   race and give wrong results. Order them on one stream.
+ * - n > XS_NOALLOC_MAX_TERMS returns XS_ERR_INVALID_VALUE; other errors as
+ *   for xs_sum_async. */
+xs_status xs_sum_noalloc(const double* d_values, int64_t n, double* d_out, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batched segmented sums (CSR)
  * ------------------------------------------------------------------------- */

@@ -529,6 +529,42 @@ xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState
   return XS_OK;
 }
 
+// Launch of the small-superaccumulator kernel of shape (384 threads, 4
+// loads) into `target`, without the per-device context: the grid is given by
+// the caller (see small_fixed_grid). Allocates nothing.
+xs_status launch_small_fixed(const double* d_values, int64_t n, AccState* target, double* d_out,
+                             int grid, cudaStream_t s) {
+  constexpr int B = 384, U = 4;
+  const long long tile_pairs = (long long)B * U;
+  const long long ntiles = std::max<long long>(1, (n / 2 + tile_pairs - 1) / tile_pairs);
+  const long long g = std::max<long long>(1, std::min<long long>(grid, ntiles));
+  SumArgs a;
+  a.x = d_values;
+  a.n = n;
+  a.g = target;
+  a.out = d_out;
+  a.mode = 0;
+  a.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * U));
+  a.prefetch = g_prefetch_tiles;
+  k_sum_small<B, U><<<(unsigned)g, B, small_smem<B>(), s>>>(a);
+  XS_TRY_CUDA(cudaGetLastError());
+  return XS_OK;
+}
+
+// One-wave grid of that shape on the current device; also raises the kernel's
+// dynamic shared-memory limit. Allocates nothing.
+xs_status small_fixed_grid(int* grid) {
+  int dev = 0, sms = 0, occ = 0;
+  XS_TRY_CUDA(cudaGetDevice(&dev));
+  XS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  XS_TRY_CUDA(cudaFuncSetAttribute(k_sum_small<384, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)small_smem<384>()));
+  XS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sum_small<384, 4>, 384,
+                                                            small_smem<384>()));
+  *grid = sms * (occ > 0 ? occ : 1);
+  return XS_OK;
+}
+
 }  // namespace xs
 
 using namespace xs;

@@ -70,6 +70,9 @@ Workspace* workspace(DeviceCtx* ctx, cudaStream_t s, xs_status* st);
 xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState* target,
                      double* d_out, int mode, SumShape shape, int grid, cudaStream_t s);
 SumShape default_shape(DeviceCtx* ctx, int64_t n);
+xs_status launch_small_fixed(const double* d_values, int64_t n, AccState* target, double* d_out,
+                             int grid, cudaStream_t s);
+xs_status small_fixed_grid(int* grid);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

@@ -62,6 +62,7 @@ _SIGS = {
     "xs_default_shape": (ctypes.c_int, [_c_int64, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "xs_sum_host": (ctypes.c_int, [_vp, _c_int64, ctypes.POINTER(ctypes.c_double), _vp]),
+    "xs_sum_noalloc": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_inexact_sum_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_autotune_sum": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -202,6 +203,14 @@ def xs_sum_host(h_values, n: int, stream=None) -> float:
     out = ctypes.c_double()
     _check(load().xs_sum_host(_ptr(h_values), n, ctypes.byref(out), _stream(stream)), "xs_sum_host")
     return out.value
+
+
+XS_NOALLOC_MAX_TERMS = 1 << 45
+
+
+def xs_sum_noalloc(d_values, n: int, d_out, stream=None) -> None:
+    _check(load().xs_sum_noalloc(_ptr(d_values), n, _ptr(d_out), _stream(stream)),
+           "xs_sum_noalloc")
 
 
 def xs_inexact_sum_async(d_values, n: int, d_out, stream=None) -> None:
