@@ -43,14 +43,26 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
-    h = hashlib.sha256()
+# Source regions that define each profiled kernel: the shared device header
+# plus the kernel's own section of its translation unit.
+KERNEL_SOURCES = {
+    "k_sum_small": ("xs_core.cu", "struct SumArgs {", "// Large superaccumulator kernel"),
+    "k_sum_large": ("xs_core.cu", "// Large superaccumulator kernel", "// Accumulator-handle kernels"),
+    "k_seg_main": ("xs_segments.cu", "struct SegArgs {", "namespace {"),
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the sources of one kernel; a profile taken on other sources is stale."""
     csrc = os.path.join(ROOT, "paper_1505_05571_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".hpp", ".cpp")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode())
-                h.update(fh.read())
+    h = hashlib.sha256()
+    with open(os.path.join(csrc, "xs_device.cuh"), "rb") as fh:
+        h.update(fh.read())
+    f, start, end = KERNEL_SOURCES[kernel]
+    with open(os.path.join(csrc, f)) as fh:
+        text = fh.read()
+    i = text.index(start)
+    h.update(text[i:text.index(end, i + len(start))].encode())
     return h.hexdigest()[:16]
 
 
@@ -64,7 +76,7 @@ def profiled_traffic(kernel: str):
     except (OSError, ValueError):
         return None
     e = d.get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
