@@ -203,6 +203,72 @@ xs_status xs_autotune_segments(const double* d_values, const int64_t* d_offsets,
                                float* best_us);
 
 /* ---------------------------------------------------------------------------
+ * Serving loop: continuous batching of sum and append requests
+ *
+ * Each request is summed exactly and rounded once (abstract); a session keeps
+ * its running exact sum in a device-resident accumulator between requests and
+ * rounds only when finished (Discussion: partial superaccumulators are added
+ * exactly). A scheduler thread admits queued requests while an accumulator
+ * slot and the byte budget allow, packs the admitted ones into one persistent
+ * batch launch per scheduling round (smallest requests first), and keeps up to
+ * `streams` batches in flight, so requests that arrive while others run join
+ * the next batch and their work overlaps on the device. Results are the same
+ * bits as the request alone.
+ * ------------------------------------------------------------------------- */
+
+typedef struct xs_server_s* xs_server;
+
+typedef struct xs_server_options {
+  int64_t budget_bytes; /* admission budget: 8 n bytes per admitted request until it completes,
+                           plus 560 B per open accumulator (0 = 40 GB) */
+  int max_sessions;     /* accumulator slots, shared by sessions and one-shot sums (0 = 4096) */
+  int streams;          /* batches in flight at once (0 = 3) */
+  int max_batch;        /* requests per batch launch (0 = 256) */
+  int tile_elems;       /* elements per block work item (0 = 262144) */
+} xs_server_options;
+
+/* xs_request.flags */
+#define XS_REQ_FINISH 1u /* after adding the data: round the session, return it, close it */
+
+typedef struct xs_request {
+  uint64_t session;       /* 0 = one-shot sum of the data; else an id from xs_server_open_session */
+  const double* d_values; /* device array, read when the request runs: keep it valid until done */
+  int64_t n;
+  uint32_t flags;         /* XS_REQ_FINISH (implied for one-shot sums) */
+  uint32_t reserved;
+} xs_request;
+
+typedef struct xs_result {
+  int32_t status;  /* XS_OK when done; XS_ERR_NOT_READY while queued or running */
+  int32_t reserved;
+  double value;    /* rounded exact sum of a one-shot or finishing request (NaN for appends) */
+  int64_t t_submit_ns, t_admit_ns, t_launch_ns, t_done_ns; /* server clock, ns since creation */
+} xs_result;
+
+typedef struct xs_server_stats {
+  int64_t submitted, completed, batches, bytes_done;
+  int64_t queued, in_flight_bytes, open_sessions;
+} xs_server_stats;
+
+/* Creates the server on the current device: allocates the slot pool and the
+ * per-stream batch buffers, starts the scheduler thread. */
+xs_status xs_server_create(xs_server* s, const xs_server_options* opts);
+/* Reserves an accumulator slot for a session (XS_ERR_BUDGET if none is free). */
+xs_status xs_server_open_session(xs_server s, uint64_t* session);
+/* Queues a request (thread-safe). Requests of one session apply in submission
+ * order. XS_ERR_BUDGET if 8 n alone exceeds the budget; XS_ERR_INVALID_POINTER
+ * for a non-device array; XS_ERR_INVALID_VALUE for an unknown or finished
+ * session. */
+xs_status xs_server_submit(xs_server s, const xs_request* r, uint64_t* request_id);
+/* Non-blocking: out->status is XS_ERR_NOT_READY until the request is done. */
+xs_status xs_server_poll(xs_server s, uint64_t request_id, xs_result* out);
+/* Blocks up to timeout_ns (< 0: no limit); XS_ERR_TIMEOUT if still not done. */
+xs_status xs_server_wait(xs_server s, uint64_t request_id, int64_t timeout_ns, xs_result* out);
+xs_status xs_server_stats_get(xs_server s, xs_server_stats* out);
+/* Waits for every queued and running request, stops the thread, frees. */
+xs_status xs_server_destroy(xs_server s);
+
+/* ---------------------------------------------------------------------------
  * Device-resident accumulators (partial sums that are merged exactly,
  * Discussion; canonical form after carry propagation, small section)
  * ------------------------------------------------------------------------- */

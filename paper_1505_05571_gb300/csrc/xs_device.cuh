@@ -218,6 +218,67 @@ __device__ __forceinline__ void sacc_propagate(long long* __restrict__ a, int st
   a[(kSChunks - 1) * stride] += carry;
 }
 
+// Adds x[lo, hi) to the per-thread accumulators of `nthr` cooperating threads
+// (rank r among them). The body streams as groups of UNROLL 16-byte vectors
+// per thread: full groups load without bounds checks into two register buffers
+// used in turn (the next group's loads are in flight while the current one is
+// added), the ragged last group is padded with -0. One unaligned head and one
+// odd tail element go to ranks 0 and nthr-1. With PREFETCH, rank 0 prefetches
+// the range into L2 a few groups ahead.
+template <int BLOCK, int UNROLL, bool PREFETCH>
+__device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x, long long lo,
+                                                 long long hi, int r, int nthr) {
+  const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(x);
+  long long p = lo;
+  if (p < hi && (((uintptr_t)(x + p)) & 15u) != 0u) {
+    if (r == 0) T.one<BLOCK>(xb[p]);
+    ++p;
+  }
+  if (((hi - p) & 1) != 0 && p < hi) {
+    if (r == nthr - 1) T.one<BLOCK>(xb[hi - 1]);
+    --hi;
+  }
+  const long long npairs = (hi - p) >> 1;
+  const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(x + p);
+  const long long gsz = (long long)UNROLL * nthr;  // pairs per group
+  const long long nfull = npairs / gsz;
+  constexpr int kAhead = 6;  // groups prefetched ahead
+  auto prefetch = [&](long long g) {
+    if (PREFETCH && r == 0 && g < nfull + 1) {
+      const long long first = g * gsz;
+      if (first < npairs) prefetch_l2(xv + first, (unsigned)(min(gsz, npairs - first) * 16));
+    }
+  };
+  auto load_full = [&](long long g, ulonglong2* buf) {
+    const ulonglong2* q = xv + g * gsz + r;
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) buf[u] = ld_stream(q + (long long)u * nthr);
+  };
+  if (PREFETCH)
+    for (int k = 1; k <= kAhead; ++k) prefetch(k);
+  ulonglong2 A[UNROLL], B[UNROLL];
+  long long g = 0;
+  if (nfull > 0) load_full(0, A);
+  while (g < nfull) {
+    prefetch(g + kAhead + 1);
+    if (g + 1 < nfull) load_full(g + 1, B);
+    T.group<BLOCK, UNROLL>(A);
+    if (++g >= nfull) break;
+    prefetch(g + kAhead + 1);
+    if (g + 1 < nfull) load_full(g + 1, A);
+    T.group<BLOCK, UNROLL>(B);
+    ++g;
+  }
+  if (nfull * gsz < npairs) {
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const long long k = nfull * gsz + (long long)u * nthr + r;
+      A[u] = k < npairs ? ld_stream(xv + k) : make_ulonglong2(kNegZero, kNegZero);
+    }
+    T.group<BLOCK, UNROLL>(A);
+  }
+}
+
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);

@@ -116,44 +116,6 @@ __global__ void __launch_bounds__(1024) k_seg_prep(SegArgs a) {
   }
 }
 
-// Adds x[lo, hi) to the per-thread accumulators of `nthr` cooperating threads
-// (rank r among them). 16-byte loads, the next group kept in flight while the
-// current one is added; one unaligned head and one odd tail element.
-template <int BLOCK, int UNROLL>
-__device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x, long long lo,
-                                                 long long hi, int r, int nthr) {
-  const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(x);
-  long long p = lo;
-  if (p < hi && (((uintptr_t)(x + p)) & 15u) != 0u) {
-    if (r == 0) T.one<BLOCK>(xb[p]);
-    ++p;
-  }
-  if (((hi - p) & 1) != 0 && p < hi) {
-    if (r == nthr - 1) T.one<BLOCK>(xb[hi - 1]);
-    --hi;
-  }
-  const long long npairs = (hi - p) >> 1;
-  const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(x + p);
-  const long long step = (long long)UNROLL * nthr;
-  ulonglong2 cur[UNROLL], nxt[UNROLL];
-  long long q = r;
-#pragma unroll
-  for (int u = 0; u < UNROLL; ++u) {
-    const long long k = q + (long long)u * nthr;
-    cur[u] = k < npairs ? ld_stream(xv + k) : make_ulonglong2(kNegZero, kNegZero);
-  }
-  for (; q < npairs; q += step) {
-#pragma unroll
-    for (int u = 0; u < UNROLL; ++u) {
-      const long long k = q + step + (long long)u * nthr;
-      nxt[u] = k < npairs ? ld_stream(xv + k) : make_ulonglong2(kNegZero, kNegZero);
-    }
-    T.group<BLOCK, UNROLL>(cur);
-#pragma unroll
-    for (int u = 0; u < UNROLL; ++u) cur[u] = nxt[u];
-  }
-}
-
 template <int BLOCK, int UNROLL>
 __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
   extern __shared__ __align__(16) long long smem_seg[];
@@ -193,7 +155,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     const long long hi = min(lo + a.tile_elems, seg_hi);
     for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
     T.reset();
-    accumulate_range<BLOCK, UNROLL>(T, a.x, lo, hi, tid, BLOCK);
+    accumulate_range<BLOCK, UNROLL, true>(T, a.x, lo, hi, tid, BLOCK);
     __syncthreads();
     unsigned f = __reduce_or_sync(kFull, T.flags());
     const unsigned long long k = warp_max_ull(T.nkey);
@@ -275,7 +237,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     }
     for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
     T.reset();
-    accumulate_range<BLOCK, 2>(T, a.x, lo, hi, lane, 32);
+    accumulate_range<BLOCK, 2, false>(T, a.x, lo, hi, lane, 32);
     __syncwarp();
     // lane L gathers chunks L, L+32, L+64 of the warp's 32 accumulators, split
     // into low and high halves; reads are rotated by lane to avoid conflicts

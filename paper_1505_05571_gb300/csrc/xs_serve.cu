@@ -1,0 +1,589 @@
+// Serving loop: continuous batching of exact-sum requests on one GPU.
+//
+// Requests (one-shot sums, session appends, session finishes) queue on the
+// host. A scheduler thread admits them while an accumulator slot and the byte
+// budget allow, packs every admitted request into one batch, and launches the
+// batch as one persistent kernel on one of `streams` CUDA streams; up to
+// `streams` batches run at once, so work submitted while others are running
+// joins the next batch and overlaps with them on the device.
+//
+// Device side, each request becomes tiles of tile_elems elements. A block sums
+// a tile with per-thread small superaccumulators (Fig. 3) and adds its partial
+// into the request's accumulator slot with integer atomics (partials add
+// exactly, Discussion). The last tile of a slot in a batch either normalises
+// the slot in place (appends: the session's exact sum stays on the device) or
+// rounds it once and clears it (finishes and one-shot sums). A session never
+// has two batches in flight, so its slot is only touched by one kernel at a
+// time, and a batch may carry several requests of one session.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "xs_host.hpp"
+
+namespace xs {
+
+struct BatchItem {
+  const double* x;
+  long long n;
+  long long tile0;     // first global tile of this item
+  int slot;            // accumulator slot
+  int slot_tiles;      // tiles of all items of this slot in the batch (ticket target)
+  int res_idx;         // result index written by the slot's finisher (-1: none)
+  unsigned flags;      // bit 0: the slot's group ends with a finish
+};
+
+struct BatchHeader {
+  unsigned long long cursor;
+  long long total_tiles;
+  int nitems;
+  int pad;
+  long long pad2;
+};
+
+struct BatchArgs {
+  const BatchItem* items;
+  BatchHeader* hdr;
+  AccState* slots;
+  unsigned long long* results;
+  long long tile_elems;
+};
+
+constexpr int kServeBlock = 192;
+constexpr int kServeUnroll = 4;
+
+template <int BLOCK, int UNROLL>
+__global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
+  extern __shared__ __align__(16) long long smem_srv[];
+  __shared__ long long s_tile;
+  __shared__ unsigned s_flags;
+  __shared__ unsigned long long s_nkey;
+  __shared__ unsigned s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  SmallThread T;
+  T.acc = smem_srv + tid;
+  const long long total = a.hdr->total_tiles;
+  const int nitems = a.hdr->nitems;
+  for (;;) {
+    if (tid == 0) {
+      s_tile = (long long)atomicAdd(&a.hdr->cursor, 1ull);
+      s_flags = 0u;
+      s_nkey = 0ull;
+    }
+    __syncthreads();
+    const long long t = s_tile;
+    if (t >= total) break;
+    int lo_i = 0, hi_i = nitems;  // last item with tile0 <= t
+    while (hi_i - lo_i > 1) {
+      const int mid = (lo_i + hi_i) >> 1;
+      if (a.items[mid].tile0 <= t) lo_i = mid; else hi_i = mid;
+    }
+    const BatchItem it = a.items[lo_i];
+    const long long first = (t - it.tile0) * a.tile_elems;
+    const long long end = min(first + a.tile_elems, it.n);
+    for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
+    T.reset();
+    if (first < end) accumulate_range<BLOCK, UNROLL, true>(T, it.x, first, end, tid, BLOCK);
+    __syncthreads();
+    unsigned f = __reduce_or_sync(kFull, T.flags());
+    const unsigned long long k = warp_max_ull(T.nkey);
+    if (lane == 0) {
+      if (f) atomicOr(&s_flags, f);
+      if (k) atomicMax(&s_nkey, k);
+    }
+    AccState* g = a.slots + it.slot;
+    unsigned long long* gc = reinterpret_cast<unsigned long long*>(g->chunk);
+    block_chunk_sums<BLOCK>(smem_srv, [&](int c, long long v) {
+      if (v != 0) atomicAdd(gc + c, (unsigned long long)v);
+    });
+    __syncthreads();
+    if (tid == 0) {
+      unsigned fl = s_flags | ((it.n > 0 && t == it.tile0) ? kFlagAny : 0u);
+      if (fl) atomicOr(&g->flags, fl);
+      if (s_nkey) atomicMax(&g->nan_key, s_nkey);
+      __threadfence();
+      s_last = (atomicAdd(&g->ticket, 1u) == (unsigned)(it.slot_tiles - 1)) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last && warp == 0) {
+      __threadfence();
+      if (it.flags & 1u) {  // round once and clear the slot
+        const long long v0 = (long long)atomicExch(gc + lane, 0ull);
+        const long long v1 = (long long)atomicExch(gc + lane + 32, 0ull);
+        const long long v2 = lane < 3 ? (long long)atomicExch(gc + lane + 64, 0ull) : 0;
+        unsigned fl = 0u;
+        unsigned long long key = 0ull;
+        if (lane == 0) {
+          fl = atomicExch(&g->flags, 0u);
+          key = atomicExch(&g->nan_key, 0ull);
+          atomicExch(&g->ticket, 0u);
+        }
+        fl = __shfl_sync(kFull, fl, 0);
+        key = __shfl_sync(kFull, key, 0);
+        const unsigned long long r = warp_round(v0, v1, v2, fl, key);
+        if (lane == 0 && it.res_idx >= 0) a.results[it.res_idx] = r;
+      } else {  // keep the exact sum, in canonical form
+        long long v0 = (long long)__ldcg(gc + lane);
+        long long v1 = (long long)__ldcg(gc + lane + 32);
+        long long v2 = lane < 3 ? (long long)__ldcg(gc + lane + 64) : 0;
+        warp_normalize(v0, v1, v2);
+        gc[lane] = (unsigned long long)v0;
+        gc[lane + 32] = (unsigned long long)v1;
+        if (lane < 3) gc[lane + 64] = (unsigned long long)v2;
+        if (lane == 0) g->ticket = 0u;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+constexpr double kNaN = __builtin_nan("");
+
+struct Request {
+  uint64_t id = 0;
+  uint64_t session = 0;
+  const double* x = nullptr;
+  int64_t n = 0;
+  bool finish = false;
+  int slot = -1;
+  int64_t t_submit = 0, t_admit = 0, t_launch = 0, t_done = 0;
+  int32_t status = XS_ERR_NOT_READY;
+  double value = kNaN;
+};
+
+struct Session {
+  int slot = -1;
+  bool finish_submitted = false;
+  bool busy = false;  // a batch holding its requests is in flight
+};
+
+struct BatchSlot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  void* d_mem = nullptr;  // header | items | results
+  void* h_mem = nullptr;  // pinned mirror
+  BatchHeader* d_hdr = nullptr;
+  BatchItem* d_items = nullptr;
+  unsigned long long* d_results = nullptr;
+  BatchHeader* h_hdr = nullptr;
+  BatchItem* h_items = nullptr;
+  unsigned long long* h_results = nullptr;
+  std::vector<Request*> reqs;
+  std::vector<uint64_t> sessions;
+  bool busy = false;
+};
+
+}  // namespace
+
+}  // namespace xs
+
+using namespace xs;
+
+struct xs_server_s {
+  int device = -1;
+  xs_server_options opt{};
+  int grid = 0;
+  AccState* d_slots = nullptr;
+  std::vector<int> free_slots;
+  std::mutex mu;
+  std::condition_variable cv_sched;
+  std::condition_variable cv_done;
+  std::deque<Request*> pending;
+  std::unordered_map<uint64_t, Request*> reqs;
+  std::unordered_map<uint64_t, Session> sessions;
+  int64_t budget_free = 0;
+  std::vector<BatchSlot> batches;
+  std::thread thr;
+  bool stop = false;
+  uint64_t next_id = 1, next_session = 1;
+  Clock::time_point t0;
+  xs_server_stats st{};
+
+  int64_t now() const {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t0).count();
+  }
+  void loop();
+  std::vector<Request*> admit_locked();
+  void launch(BatchSlot& b);
+  void complete_locked(BatchSlot& b, bool ok);
+};
+
+std::vector<Request*> xs_server_s::admit_locked() {
+  std::vector<Request*> out;
+  std::unordered_set<uint64_t> blocked;  // sessions whose earlier request must go first
+  for (auto it = pending.begin(); it != pending.end() && (int)out.size() < opt.max_batch;) {
+    Request* r = *it;
+    if (r->session != 0) {
+      Session& S = sessions[r->session];
+      if (S.busy || blocked.count(r->session)) {
+        blocked.insert(r->session);
+        ++it;
+        continue;
+      }
+    }
+    const int64_t need = r->n * 8 + (r->session == 0 ? (int64_t)sizeof(AccState) : 0);
+    if (need > budget_free || (r->session == 0 && free_slots.empty())) {
+      if (r->session != 0) blocked.insert(r->session);
+      ++it;
+      continue;
+    }
+    budget_free -= need;
+    if (r->session == 0) {
+      r->slot = free_slots.back();
+      free_slots.pop_back();
+    } else {
+      r->slot = sessions[r->session].slot;
+    }
+    r->t_admit = now();
+    out.push_back(r);
+    it = pending.erase(it);
+  }
+  return out;
+}
+
+void xs_server_s::launch(BatchSlot& b) {
+  // groups: the requests of one slot, in submission order; smallest groups first
+  std::map<int, std::vector<int>> by_slot;
+  for (int k = 0; k < (int)b.reqs.size(); ++k) by_slot[b.reqs[k]->slot].push_back(k);
+  std::vector<std::pair<int64_t, int>> order;
+  for (auto& kv : by_slot) {
+    int64_t tot = 0;
+    for (int k : kv.second) tot += b.reqs[k]->n;
+    order.push_back({tot, kv.first});
+  }
+  std::sort(order.begin(), order.end());
+  long long tile0 = 0;
+  int ni = 0;
+  const long long te = opt.tile_elems;
+  for (auto& o : order) {
+    const std::vector<int>& g = by_slot[o.second];
+    int slot_tiles = 0;
+    for (int k : g) slot_tiles += (int)std::max<long long>(1, (b.reqs[k]->n + te - 1) / te);
+    const Request* last = b.reqs[g.back()];
+    const bool fin = last->finish;
+    for (int k : g) {
+      const Request* r = b.reqs[k];
+      BatchItem& it = b.h_items[ni++];
+      it.x = r->x;
+      it.n = r->n;
+      it.tile0 = tile0;
+      it.slot = r->slot;
+      it.slot_tiles = slot_tiles;
+      it.res_idx = fin ? g.back() : -1;
+      it.flags = fin ? 1u : 0u;
+      tile0 += std::max<long long>(1, (r->n + te - 1) / te);
+    }
+  }
+  b.h_hdr->cursor = 0ull;
+  b.h_hdr->total_tiles = tile0;
+  b.h_hdr->nitems = ni;
+  const size_t bytes = sizeof(BatchHeader) + (size_t)ni * sizeof(BatchItem);
+  cudaError_t e = cudaMemcpyAsync(b.d_mem, b.h_mem, bytes, cudaMemcpyHostToDevice, b.stream);
+  BatchArgs a;
+  a.items = b.d_items;
+  a.hdr = b.d_hdr;
+  a.slots = d_slots;
+  a.results = b.d_results;
+  a.tile_elems = te;
+  const long long g = std::max<long long>(1, std::min<long long>(grid, tile0));
+  if (e == cudaSuccess) {
+    k_serve_batch<kServeBlock, kServeUnroll>
+        <<<(unsigned)g, kServeBlock, (size_t)kServeBlock * kSChunks * sizeof(long long), b.stream>>>(a);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b.h_results, b.d_results, b.reqs.size() * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, b.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b.done, b.stream);
+  const int64_t tl = now();
+  std::lock_guard<std::mutex> lk(mu);
+  for (Request* r : b.reqs) r->t_launch = tl;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    complete_locked(b, false);
+  }
+}
+
+void xs_server_s::complete_locked(BatchSlot& b, bool ok) {
+  const int64_t td = now();
+  for (int k = 0; k < (int)b.reqs.size(); ++k) {
+    Request* r = b.reqs[k];
+    r->t_done = td;
+    r->status = ok ? XS_OK : XS_ERR_CUDA;
+    if (r->finish && ok) std::memcpy(&r->value, &b.h_results[k], sizeof(double));
+    budget_free += r->n * 8;
+    if (r->session == 0) {
+      budget_free += (int64_t)sizeof(AccState);
+      free_slots.push_back(r->slot);
+    } else if (r->finish) {
+      auto it = sessions.find(r->session);
+      if (it != sessions.end()) {
+        free_slots.push_back(it->second.slot);
+        budget_free += (int64_t)sizeof(AccState);
+        sessions.erase(it);
+        st.open_sessions--;
+      }
+    }
+    st.completed++;
+    st.bytes_done += r->n * 8;
+    st.in_flight_bytes -= r->n * 8;
+  }
+  for (uint64_t s : b.sessions) {
+    auto it = sessions.find(s);
+    if (it != sessions.end()) it->second.busy = false;
+  }
+  b.reqs.clear();
+  b.sessions.clear();
+  b.busy = false;
+  cv_done.notify_all();
+}
+
+void xs_server_s::loop() {
+  cudaSetDevice(device);
+  std::unique_lock<std::mutex> lk(mu);
+  for (;;) {
+    bool progress = false;
+    for (BatchSlot& b : batches) {
+      if (!b.busy) continue;
+      const cudaError_t q = cudaEventQuery(b.done);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) cudaGetLastError();
+      complete_locked(b, q == cudaSuccess);
+      progress = true;
+    }
+    for (BatchSlot& b : batches) {
+      if (b.busy || pending.empty()) continue;
+      std::vector<Request*> adm = admit_locked();
+      if (adm.empty()) break;
+      b.reqs = adm;
+      b.busy = true;
+      for (Request* r : adm) {
+        if (r->session != 0) {
+          Session& S = sessions[r->session];
+          if (!S.busy) b.sessions.push_back(r->session);
+          S.busy = true;
+        }
+        st.in_flight_bytes += r->n * 8;
+      }
+      st.batches++;
+      st.queued = (int64_t)pending.size();
+      lk.unlock();
+      launch(b);
+      lk.lock();
+      progress = true;
+    }
+    bool any_busy = false;
+    for (BatchSlot& b : batches) any_busy = any_busy || b.busy;
+    if (stop && pending.empty() && !any_busy) break;
+    if (!progress) {
+      if (any_busy) {
+        cv_sched.wait_for(lk, std::chrono::microseconds(20));
+      } else {
+        cv_sched.wait(lk, [&] { return stop || !pending.empty(); });
+      }
+    }
+  }
+}
+
+extern "C" {
+
+xs_status xs_server_create(xs_server* out, const xs_server_options* opts) {
+  if (out == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  xs_status st;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  xs_server_options o{};
+  if (opts) o = *opts;
+  if (o.budget_bytes == 0) o.budget_bytes = int64_t(40) << 30;
+  if (o.max_sessions == 0) o.max_sessions = 4096;
+  if (o.streams == 0) o.streams = 3;
+  if (o.max_batch == 0) o.max_batch = 256;
+  if (o.tile_elems == 0) o.tile_elems = 1 << 18;
+  if (o.budget_bytes < 0 || o.max_sessions < 1 || o.streams < 1 || o.streams > 16 ||
+      o.max_batch < 1 || o.tile_elems < 2 * kServeBlock || (long long)o.tile_elems > 2040LL * kServeBlock)
+    return set_error(XS_ERR_INVALID_VALUE);
+  xs_server s = new xs_server_s();
+  s->device = ctx->device;
+  s->opt = o;
+  s->budget_free = o.budget_bytes;
+  s->t0 = Clock::now();
+  auto fail = [&](cudaError_t e) {
+    for (BatchSlot& b : s->batches) {
+      if (b.stream) cudaStreamDestroy(b.stream);
+      if (b.done) cudaEventDestroy(b.done);
+      if (b.d_mem) cudaFree(b.d_mem);
+      if (b.h_mem) cudaFreeHost(b.h_mem);
+    }
+    if (s->d_slots) cudaFree(s->d_slots);
+    delete s;
+    return from_cuda(e);
+  };
+  const size_t smem = (size_t)kServeBlock * kSChunks * sizeof(long long);
+  cudaError_t e = cudaFuncSetAttribute(k_serve_batch<kServeBlock, kServeUnroll>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve_batch<kServeBlock, kServeUnroll>,
+                                                      kServeBlock, smem);
+  if (e != cudaSuccess) return fail(e);
+  s->grid = ctx->num_sms * std::max(1, occ);
+  e = cudaMalloc(&s->d_slots, (size_t)o.max_sessions * sizeof(AccState));
+  if (e == cudaSuccess) e = cudaMemset(s->d_slots, 0, (size_t)o.max_sessions * sizeof(AccState));
+  if (e != cudaSuccess) return fail(e);
+  for (int k = o.max_sessions - 1; k >= 0; --k) s->free_slots.push_back(k);
+  s->batches.resize(o.streams);
+  const size_t items_bytes = (size_t)o.max_batch * sizeof(BatchItem);
+  const size_t res_bytes = (size_t)o.max_batch * sizeof(unsigned long long);
+  const size_t total = sizeof(BatchHeader) + items_bytes + res_bytes;
+  for (BatchSlot& b : s->batches) {
+    e = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_mem, total);
+    if (e == cudaSuccess) e = cudaMallocHost(&b.h_mem, total);
+    if (e != cudaSuccess) return fail(e);
+    char* d = static_cast<char*>(b.d_mem);
+    char* h = static_cast<char*>(b.h_mem);
+    b.d_hdr = reinterpret_cast<BatchHeader*>(d);
+    b.d_items = reinterpret_cast<BatchItem*>(d + sizeof(BatchHeader));
+    b.d_results = reinterpret_cast<unsigned long long*>(d + sizeof(BatchHeader) + items_bytes);
+    b.h_hdr = reinterpret_cast<BatchHeader*>(h);
+    b.h_items = reinterpret_cast<BatchItem*>(h + sizeof(BatchHeader));
+    b.h_results = reinterpret_cast<unsigned long long*>(h + sizeof(BatchHeader) + items_bytes);
+  }
+  s->thr = std::thread([s] { s->loop(); });
+  *out = s;
+  return set_error(XS_OK);
+}
+
+xs_status xs_server_open_session(xs_server s, uint64_t* session) {
+  if (s == nullptr || session == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->free_slots.empty() || s->budget_free < (int64_t)sizeof(AccState))
+    return set_error(XS_ERR_BUDGET);
+  Session S;
+  S.slot = s->free_slots.back();
+  s->free_slots.pop_back();
+  s->budget_free -= (int64_t)sizeof(AccState);
+  const uint64_t id = s->next_session++;
+  s->sessions[id] = S;
+  s->st.open_sessions++;
+  *session = id;
+  return set_error(XS_OK);
+}
+
+xs_status xs_server_submit(xs_server s, const xs_request* r, uint64_t* request_id) {
+  if (s == nullptr || r == nullptr || request_id == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  if (r->n < 0) return set_error(XS_ERR_INVALID_VALUE);
+  if (r->n > 0) {
+    if (((uintptr_t)r->d_values & 7u) != 0u) return set_error(XS_ERR_INVALID_VALUE);
+    const xs_status st = check_device_ptr(r->d_values);
+    if (st != XS_OK) return st;
+  }
+  const int64_t need = r->n * 8 + (r->session == 0 ? (int64_t)sizeof(AccState) : 0);
+  if (need > s->opt.budget_bytes) return set_error(XS_ERR_BUDGET);
+  Request* q = new Request();
+  q->session = r->session;
+  q->x = r->d_values;
+  q->n = r->n;
+  q->finish = (r->session == 0) || (r->flags & XS_REQ_FINISH);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (r->session != 0) {
+      auto it = s->sessions.find(r->session);
+      if (it == s->sessions.end() || it->second.finish_submitted) {
+        delete q;
+        return set_error(XS_ERR_INVALID_VALUE);
+      }
+      if (q->finish) it->second.finish_submitted = true;
+    }
+    q->id = s->next_id++;
+    q->t_submit = s->now();
+    s->pending.push_back(q);
+    s->reqs[q->id] = q;
+    s->st.submitted++;
+    s->st.queued = (int64_t)s->pending.size();
+    *request_id = q->id;
+  }
+  s->cv_sched.notify_one();
+  return set_error(XS_OK);
+}
+
+static void fill_result(const Request* q, xs_result* out) {
+  out->status = q->status;
+  out->reserved = 0;
+  out->value = q->value;
+  out->t_submit_ns = q->t_submit;
+  out->t_admit_ns = q->t_admit;
+  out->t_launch_ns = q->t_launch;
+  out->t_done_ns = q->t_done;
+}
+
+xs_status xs_server_poll(xs_server s, uint64_t request_id, xs_result* out) {
+  if (s == nullptr || out == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(request_id);
+  if (it == s->reqs.end()) return set_error(XS_ERR_INVALID_VALUE);
+  fill_result(it->second, out);
+  return set_error(XS_OK);
+}
+
+xs_status xs_server_wait(xs_server s, uint64_t request_id, int64_t timeout_ns, xs_result* out) {
+  if (s == nullptr || out == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(request_id);
+  if (it == s->reqs.end()) return set_error(XS_ERR_INVALID_VALUE);
+  Request* q = it->second;
+  auto done = [&] { return q->status != XS_ERR_NOT_READY; };
+  if (timeout_ns < 0) {
+    s->cv_done.wait(lk, done);
+  } else if (!s->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), done)) {
+    fill_result(q, out);
+    return set_error(XS_ERR_TIMEOUT);
+  }
+  fill_result(q, out);
+  return set_error(XS_OK);
+}
+
+xs_status xs_server_stats_get(xs_server s, xs_server_stats* out) {
+  if (s == nullptr || out == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->st;
+  out->queued = (int64_t)s->pending.size();
+  return set_error(XS_OK);
+}
+
+xs_status xs_server_destroy(xs_server s) {
+  if (s == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_sched.notify_all();
+  if (s->thr.joinable()) s->thr.join();
+  for (BatchSlot& b : s->batches) {
+    cudaStreamSynchronize(b.stream);
+    cudaStreamDestroy(b.stream);
+    cudaEventDestroy(b.done);
+    cudaFree(b.d_mem);
+    cudaFreeHost(b.h_mem);
+  }
+  cudaFree(s->d_slots);
+  for (auto& kv : s->reqs) delete kv.second;
+  delete s;
+  return set_error(XS_OK);
+}
+
+}  // extern "C"

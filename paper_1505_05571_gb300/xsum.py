@@ -47,6 +47,29 @@ class xs_seg_options(ctypes.Structure):
                 ("short_max", ctypes.c_int), ("carry_tiles", ctypes.c_int)]
 
 
+class xs_server_options(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_sessions", ctypes.c_int),
+                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("tile_elems", ctypes.c_int)]
+
+
+class xs_request(ctypes.Structure):
+    _fields_ = [("session", ctypes.c_uint64), ("d_values", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class xs_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("value", ctypes.c_double),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_launch_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+
+
+class xs_server_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "batches", "bytes_done",
+                                              "queued", "in_flight_bytes", "open_sessions")]
+
+
+XS_REQ_FINISH = 1
+
 # name: (restype, argtypes)
 _SIGS = {
     "xs_version": (ctypes.c_char_p, []),
@@ -77,6 +100,13 @@ _SIGS = {
     "xs_autotune_segments": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, ctypes.c_int, _vp,
                                             ctypes.POINTER(xs_seg_options),
                                             ctypes.POINTER(ctypes.c_float)]),
+    "xs_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(xs_server_options)]),
+    "xs_server_open_session": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "xs_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(xs_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "xs_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(xs_result)]),
+    "xs_server_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(xs_result)]),
+    "xs_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(xs_server_stats)]),
+    "xs_server_destroy": (ctypes.c_int, [_vp]),
     "xs_acc_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp]),
     "xs_acc_init": (ctypes.c_int, [_vp, _vp]),
     "xs_acc_add": (ctypes.c_int, [_vp, _vp, _c_int64, _vp]),
@@ -322,3 +352,51 @@ def xs_acc_device_state(h: int) -> int:
 def acc_state_chunks(state: bytes) -> list[int]:
     """The 67 signed chunks of an exported state (little-endian int64)."""
     return list(struct.unpack("<67q", state[:536]))
+
+
+def _result_dict(r: xs_result) -> dict:
+    return {"status": r.status, "value": r.value, "t_submit_ns": r.t_submit_ns,
+            "t_admit_ns": r.t_admit_ns, "t_launch_ns": r.t_launch_ns, "t_done_ns": r.t_done_ns}
+
+
+def xs_server_create(budget_bytes: int = 0, max_sessions: int = 0, streams: int = 0,
+                     max_batch: int = 0, tile_elems: int = 0) -> int:
+    o = xs_server_options(budget_bytes, max_sessions, streams, max_batch, tile_elems)
+    h = _vp()
+    _check(load().xs_server_create(ctypes.byref(h), ctypes.byref(o)), "xs_server_create")
+    return h.value
+
+
+def xs_server_open_session(server: int) -> int:
+    sid = ctypes.c_uint64()
+    _check(load().xs_server_open_session(server, ctypes.byref(sid)), "xs_server_open_session")
+    return sid.value
+
+
+def xs_server_submit(server: int, d_values, n: int, session: int = 0, flags: int = 0) -> int:
+    req = xs_request(session, _ptr(d_values), n, flags, 0)
+    rid = ctypes.c_uint64()
+    _check(load().xs_server_submit(server, ctypes.byref(req), ctypes.byref(rid)), "xs_server_submit")
+    return rid.value
+
+
+def xs_server_poll(server: int, request_id: int) -> dict:
+    r = xs_result()
+    _check(load().xs_server_poll(server, request_id, ctypes.byref(r)), "xs_server_poll")
+    return _result_dict(r)
+
+
+def xs_server_wait(server: int, request_id: int, timeout_ns: int = -1) -> dict:
+    r = xs_result()
+    _check(load().xs_server_wait(server, request_id, timeout_ns, ctypes.byref(r)), "xs_server_wait")
+    return _result_dict(r)
+
+
+def xs_server_stats_get(server: int) -> dict:
+    st = xs_server_stats()
+    _check(load().xs_server_stats_get(server, ctypes.byref(st)), "xs_server_stats_get")
+    return {f: getattr(st, f) for f, _ in xs_server_stats._fields_}
+
+
+def xs_server_destroy(server: int) -> None:
+    _check(load().xs_server_destroy(server), "xs_server_destroy")
