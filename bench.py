@@ -199,6 +199,195 @@ def run_reference(args):
     return 0
 
 
+def med_time(torch, stream, fn, reps=20, warm=3):
+    """Median CUDA-event time (ms) of fn on `stream`."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for _ in range(warm):
+        fn()
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ts = sorted(a.elapsed_time(b) for a, b in ev)
+    return ts[len(ts) // 2]
+
+
+def extra_configs(torch, np, xsum, devgen, W, dev, stream, rate_gbs, xd, n):
+    """The other configurations, measured outside the headline's timed region."""
+    out = {}
+    f2b = lambda v: int(np.array([v]).view(np.uint64)[0])  # noqa: E731
+    bits = lambda t: int(t.view(torch.int64).item()) & ((1 << 64) - 1)  # noqa: E731
+    res = torch.empty(1, dtype=torch.float64, device=dev)
+
+    # the paper's large superaccumulator method on the same array
+    t_large = med_time(torch, stream, lambda: xsum.xs_sum_async(xd, n, res, xsum.XS_METHOD_LARGE, stream))
+    out["large_method_cfg1"] = {"us": round(t_large * 1000, 2),
+                                "gbs": round(8 * n / (t_large * 1e-3) / 1e9, 1)}
+
+    # cfg0: n = 10,000 with heavy cancellation -- latency
+    x0 = torch.from_numpy(W.cfg0_cancel(0)).to(dev)
+    t_dev = med_time(torch, stream, lambda: xsum.xs_sum_async(x0, x0.numel(), res, 0, stream), reps=50)
+    host = []
+    for _ in range(50):
+        t0 = time.perf_counter()
+        xsum.xs_sum(x0, x0.numel(), stream)
+        host.append(time.perf_counter() - t0)
+    host.sort()
+    out["cfg0_cancel_n1e4"] = {"device_us": round(t_dev * 1000, 2),
+                               "blocking_call_us_median": round(host[len(host) // 2] * 1e6, 2)}
+
+    # cfg2: adversarial arrays of 2^28 values
+    m = 1 << 28
+    y = torch.empty(m, dtype=torch.int64, device=dev)
+    c2 = {}
+    for name, fn in (("2a_full_exponent_range", devgen.full_range), ("2a_paired_cancel", devgen.paired),
+                     ("2b_cancel_1e300", devgen.cancel)):
+        fn(y, 0, 0)
+        t = med_time(torch, stream, lambda: xsum.xs_sum_async(y.view(torch.float64), m, res, 0, stream), reps=10)
+        c2[name] = {"us": round(t * 1000, 1), "gbs": round(8 * m / (t * 1e-3) / 1e9, 1)}
+    del y
+    z = torch.full((10 ** 8,), 0.1, dtype=torch.float64, device=dev)
+    t = med_time(torch, stream, lambda: xsum.xs_sum_async(z, z.numel(), res, 0, stream), reps=10)
+    c2["2c_1e8_copies_of_0.1"] = {"us": round(t * 1000, 1), "gbs": round(8e8 / (t * 1e-3) / 1e9, 1),
+                                  "exact": bits(res) == f2b(0.1 * 10 ** 8)}
+    del z
+    out["cfg2_adversarial"] = c2
+
+    # cfg3: 100,000 CSR segments, lengths log-uniform in [1, 1e6]
+    nseg = 100_000
+    lengths = W.cfg3_lengths(0, nseg, 10 ** 6)
+    off = W.cfg3_offsets(lengths)
+    total = int(off[-1])
+    free, _ = torch.cuda.mem_get_info(dev)
+    if total * 8 < free - (6 << 30):
+        v = torch.empty(total, dtype=torch.int64, device=dev)
+        devgen.band(v, 0, 0, -30, 30)
+        vd = v.view(torch.float64)
+        od = torch.from_numpy(off).to(dev)
+        so = torch.empty(nseg, dtype=torch.float64, device=dev)
+        plan = xsum.xs_seg_plan_create(vd, od, nseg, so, None, stream)
+        t_seg = med_time(torch, stream, lambda: xsum.xs_seg_plan_launch(plan, stream), reps=10)
+        xsum.xs_seg_plan_destroy(plan)
+        ref = so.clone()
+        lib = xsum.load()
+        base, ob, offs = vd.data_ptr(), so.data_ptr(), off.tolist()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(nseg):
+            lib.xs_sum_async(base + 8 * offs[k], offs[k + 1] - offs[k], ob + 8 * k, 0, stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        t_loop = time.perf_counter() - t0
+        out["cfg3_segmented"] = {
+            "segments": nseg, "values": total, "gb": round(total * 8 / 1e9, 2),
+            "ms": round(t_seg, 3), "gbs": round(total * 8 / (t_seg * 1e-3) / 1e9, 1),
+            "kernel_launches_per_call": 2, "graph": True,
+            "one_launch_per_segment_ms": round(t_loop * 1000, 1),
+            "speedup_vs_one_launch_per_segment": round(t_loop * 1000 / t_seg, 1),
+            "same_bits_as_one_launch_per_segment": bool(torch.equal(ref.view(torch.int64), so.view(torch.int64))),
+        }
+        del v, vd
+        torch.cuda.empty_cache()
+    else:
+        out["cfg3_segmented"] = {"skipped": f"needs {total * 8 / 2**30:.1f} GiB free"}
+
+    out["cfg4_serving"] = serving_report(torch, np, xsum, devgen, dev, stream, rate_gbs)
+    return out
+
+
+def serving_report(torch, np, xsum, devgen, dev, stream, rate_gbs, n_arrivals=4000, seed=7):
+    """Poisson arrivals of one-shot sums and sessions (Geometric(mean 4) appends, then a
+    finish), request sizes log-uniform 1e3..1e8 doubles, values from three workload recipes,
+    40 GB admission budget; p50/p99 latency (arrival to result) per offered load."""
+    R = 1 << 27
+    arena = torch.empty(3 * R, dtype=torch.int64, device=dev)
+    devgen.band(arena[:R], 3, 0, -40, 40)       # config-0 magnitudes
+    devgen.band(arena[R:2 * R], 4, 0, -60, 60)  # config-1
+    devgen.paired(arena[2 * R:], 5, 0)          # config-2 (paired cancellation)
+    base = arena.data_ptr()
+    rng = np.random.default_rng(seed)
+    arrivals = []  # list of list of (ptr, n)
+    for _ in range(n_arrivals):
+        g = 1 if rng.random() < 0.5 else int(rng.geometric(0.25))
+        reqs = []
+        for _ in range(g):
+            nn = int(np.exp(rng.uniform(np.log(1e3), np.log(1e8))))
+            region = int(rng.integers(0, 3))
+            o = int(rng.integers(0, R - nn))
+            reqs.append((base + 8 * (region * R + o), nn))
+        arrivals.append(reqs)
+    sizes = [sum(n for _, n in a) for a in arrivals]
+    total_bytes = 8 * sum(sizes)
+    mean_bytes = total_bytes / n_arrivals
+
+    def trace(load):
+        if load is None:
+            times = np.zeros(n_arrivals)
+        else:
+            lam = load * rate_gbs * 1e9 / mean_bytes
+            times = np.cumsum(rng.exponential(1.0 / lam, n_arrivals))
+        items, last_idx = [], []
+        for k, (t, a) in enumerate(zip(times, arrivals)):
+            tag = 0 if len(a) == 1 else k + 1
+            for j, (p, nn) in enumerate(a):
+                fl = xsum.XS_REQ_FINISH if (tag and j == len(a) - 1) else 0
+                items.append((int(t * 1e9), tag, p, nn, fl))
+            last_idx.append(len(items) - 1)
+        return times, items, last_idx
+
+    def run(load):
+        times, items, last_idx = trace(load)
+        srv = xsum.xs_server_create(budget_bytes=40 << 30, streams=3)
+        ids, start = xsum.xs_server_replay(srv, items)
+        res = [xsum.xs_server_wait(srv, ids[i], 120_000_000_000) for i in last_idx]
+        stats = xsum.xs_server_stats_get(srv)
+        xsum.xs_server_destroy(srv)
+        lat = np.array([r["t_done_ns"] - (start + int(t * 1e9)) for r, t in zip(res, times)]) / 1e6
+        span = (max(r["t_done_ns"] for r in res) - start) / 1e9
+        return res, lat, span, stats
+
+    report = {"arrivals": n_arrivals, "requests": sum(len(a) for a in arrivals),
+              "mean_request_mb": round(8 * np.mean([n for a in arrivals for _, n in a]) / 1e6, 2),
+              "budget_gb": 40, "streams": 3, "loads": {}}
+    for load in (0.5, 0.8, 1.0):
+        _, lat, span, stats = run(load)
+        report["loads"][str(load)] = {
+            "offered_gbs": round(load * rate_gbs, 1), "achieved_gbs": round(total_bytes / span / 1e9, 1),
+            "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "batches": stats["batches"]}
+    res, lat, span, stats = run(None)
+    report["saturated"] = {"gbs": round(total_bytes / span / 1e9, 1),
+                           "arrivals_per_s": round(n_arrivals / span, 1), "batches": stats["batches"],
+                           "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                           "p99_ms": round(float(np.percentile(lat, 99)), 3)}
+    # serial one-at-a-time through the plain API (also the "alone" result of each arrival)
+    out1 = torch.empty(1, dtype=torch.float64, device=dev)
+    same = True
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for a, r in zip(arrivals, res):
+        if len(a) == 1:
+            p, nn = a[0]
+            xsum.xs_sum_async(p, nn, out1, 0, stream)
+        else:
+            h = xsum.xs_acc_create(stream)
+            for p, nn in a:
+                xsum.xs_acc_add(h, p, nn, stream)
+            xsum.xs_acc_round(h, out1, stream)
+        v = out1.item()
+        if len(a) > 1:
+            xsum.xs_acc_destroy(h)
+        same = same and (np.array([v]).view(np.int64)[0] == np.array([r["value"]]).view(np.int64)[0])
+    t_serial = time.perf_counter() - t0
+    report["serial_one_at_a_time"] = {"gbs": round(total_bytes / t_serial / 1e9, 1),
+                                      "arrivals_per_s": round(n_arrivals / t_serial, 1)}
+    report["all_results_equal_alone"] = bool(same)
+    del arena
+    torch.cuda.empty_cache()
+    return report
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -236,21 +425,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
 
     # inexact device sums on the same tensor (comparison only)
-    def med_time(fn, reps=20):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(reps)]
-        for _ in range(5):
-            fn()
-        for a, b in ev:
-            a.record(stream)
-            fn()
-            b.record(stream)
-        torch.cuda.synchronize(dev)
-        ts = sorted(a.elapsed_time(b) for a, b in ev)
-        return ts[len(ts) // 2]
-
-    t_torch = med_time(lambda: torch.sum(xd))
-    t_inexact = med_time(lambda: xsum.xs_inexact_sum_async(xd, n, out, stream))
+    t_torch = med_time(torch, stream, lambda: torch.sum(xd))
+    t_inexact = med_time(torch, stream, lambda: xsum.xs_inexact_sum_async(xd, n, out, stream))
 
     if world > 1:
         import torch.distributed as dist
@@ -351,6 +527,9 @@ def run_ours(args):
         "clocks": clk.summary(),
         "result_bits": f"{bits_last & ((1 << 64) - 1):#018x}",
     }
+    if not args.no_extras:
+        import workloads as W
+        line["configs"] = extra_configs(torch, np, xsum, devgen, W, dev, stream, gbs_one, xd, n)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_run()
     print(json.dumps(line), flush=True)
@@ -368,6 +547,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations (segmented, serving, latency, adversarial)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

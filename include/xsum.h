@@ -265,6 +265,26 @@ xs_status xs_server_poll(xs_server s, uint64_t request_id, xs_result* out);
 /* Blocks up to timeout_ns (< 0: no limit); XS_ERR_TIMEOUT if still not done. */
 xs_status xs_server_wait(xs_server s, uint64_t request_id, int64_t timeout_ns, xs_result* out);
 xs_status xs_server_stats_get(xs_server s, xs_server_stats* out);
+
+/* One request of a replayed arrival trace. */
+typedef struct xs_replay_item {
+  int64_t t_ns;           /* submit time, ns after the replay starts (non-decreasing) */
+  uint64_t session_tag;   /* 0 = one-shot sum; else items with the same tag form one session,
+                             opened at its first item */
+  const double* d_values; /* device array */
+  int64_t n;
+  uint32_t flags;         /* XS_REQ_FINISH on a session's last item */
+  uint32_t reserved;
+} xs_replay_item;
+
+/* Submits items[0..count) at their times from the calling thread (a load
+ * generator that keeps microsecond timing, which a scripting language cannot),
+ * writing each request id. *start_ns receives the replay start on the server
+ * clock, so item k arrived at *start_ns + items[k].t_ns. Opening a session
+ * waits up to 60 s for a free slot (XS_ERR_TIMEOUT after that). Returns after
+ * the last submit; collect results with xs_server_wait. */
+xs_status xs_server_replay(xs_server s, const xs_replay_item* items, int64_t count,
+                           uint64_t* request_ids, int64_t* start_ns);
 /* Waits for every queued and running request, stops the thread, frees. */
 xs_status xs_server_destroy(xs_server s);
 

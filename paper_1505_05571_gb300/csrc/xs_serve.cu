@@ -565,6 +565,53 @@ xs_status xs_server_stats_get(xs_server s, xs_server_stats* out) {
   return set_error(XS_OK);
 }
 
+xs_status xs_server_replay(xs_server s, const xs_replay_item* items, int64_t count,
+                           uint64_t* request_ids, int64_t* start_ns) {
+  if (s == nullptr || (count > 0 && (items == nullptr || request_ids == nullptr)))
+    return set_error(XS_ERR_INVALID_POINTER);
+  if (count < 0) return set_error(XS_ERR_INVALID_VALUE);
+  std::unordered_map<uint64_t, uint64_t> open;  // tag -> session id
+  const Clock::time_point t_start = Clock::now();
+  if (start_ns) *start_ns = s->now();
+  for (int64_t k = 0; k < count; ++k) {
+    const xs_replay_item& it = items[k];
+    const Clock::time_point due = t_start + std::chrono::nanoseconds(it.t_ns);
+    for (;;) {  // sleep while far, spin for the last stretch
+      const auto left = due - Clock::now();
+      if (left <= std::chrono::nanoseconds(0)) break;
+      if (left > std::chrono::microseconds(200)) std::this_thread::sleep_for(left / 2);
+    }
+    xs_request r{};
+    r.d_values = it.d_values;
+    r.n = it.n;
+    r.flags = it.flags;
+    if (it.session_tag != 0) {
+      auto o = open.find(it.session_tag);
+      if (o == open.end()) {
+        uint64_t sid = 0;
+        const Clock::time_point give_up = Clock::now() + std::chrono::seconds(60);
+        for (;;) {
+          const xs_status st = xs_server_open_session(s, &sid);
+          if (st == XS_OK) break;
+          if (st != XS_ERR_BUDGET || Clock::now() > give_up)
+            return set_error(st == XS_ERR_BUDGET ? XS_ERR_TIMEOUT : st);
+          std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        o = open.emplace(it.session_tag, sid).first;
+      }
+      r.session = o->second;
+      if (it.flags & XS_REQ_FINISH) {
+        const uint64_t sid = o->second;
+        open.erase(o);
+        r.session = sid;
+      }
+    }
+    const xs_status st = xs_server_submit(s, &r, &request_ids[k]);
+    if (st != XS_OK) return st;
+  }
+  return set_error(XS_OK);
+}
+
 xs_status xs_server_destroy(xs_server s) {
   if (s == nullptr) return set_error(XS_ERR_INVALID_POINTER);
   {

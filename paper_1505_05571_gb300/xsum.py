@@ -68,6 +68,12 @@ class xs_server_stats(ctypes.Structure):
                                               "queued", "in_flight_bytes", "open_sessions")]
 
 
+class xs_replay_item(ctypes.Structure):
+    _fields_ = [("t_ns", ctypes.c_int64), ("session_tag", ctypes.c_uint64),
+                ("d_values", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 XS_REQ_FINISH = 1
 
 # name: (restype, argtypes)
@@ -107,6 +113,8 @@ _SIGS = {
     "xs_server_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(xs_result)]),
     "xs_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(xs_server_stats)]),
     "xs_server_destroy": (ctypes.c_int, [_vp]),
+    "xs_server_replay": (ctypes.c_int, [_vp, ctypes.POINTER(xs_replay_item), ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int64)]),
     "xs_acc_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp]),
     "xs_acc_init": (ctypes.c_int, [_vp, _vp]),
     "xs_acc_add": (ctypes.c_int, [_vp, _vp, _c_int64, _vp]),
@@ -400,3 +408,15 @@ def xs_server_stats_get(server: int) -> dict:
 
 def xs_server_destroy(server: int) -> None:
     _check(load().xs_server_destroy(server), "xs_server_destroy")
+
+
+def xs_server_replay(server: int, items) -> tuple[list[int], int]:
+    """items: sequence of (t_ns, session_tag, d_values_ptr, n, flags). Returns (ids, start_ns)."""
+    arr = (xs_replay_item * len(items))()
+    for k, (t, tag, ptr, n, fl) in enumerate(items):
+        arr[k] = xs_replay_item(int(t), int(tag), int(ptr), int(n), int(fl), 0)
+    ids = (ctypes.c_uint64 * len(items))()
+    start = ctypes.c_int64()
+    _check(load().xs_server_replay(server, arr, len(items), ids, ctypes.byref(start)),
+           "xs_server_replay")
+    return list(ids), start.value
