@@ -133,6 +133,21 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def max_over_ranks(torch, value: float, device) -> float:
+    """Largest value over all ranks (identity on one process)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_per_rank: float, world: int, slowest_seconds: float) -> float:
+    """Whole-job throughput: the bytes every rank summed over the slowest rank's time."""
+    return bytes_per_rank * world / slowest_seconds / 1e9
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -439,12 +454,7 @@ def run_ours(args):
             step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(torch, e0.elapsed_time(e1), dev)
     ms_step = ms_total / args.steps
 
     # the result of the last step, checked against the first (determinism)
@@ -460,12 +470,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         r = xsum.xs_sum_host(hd, n, stream)
-    t_e2e = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(torch, (time.perf_counter() - t0) / e2e_steps, dev)
     same = (np.array([r0, r]).view(np.int64) == bits_last).all()
 
     if rank != 0:
@@ -474,7 +479,7 @@ def run_ours(args):
 
     peak, peak_kind = read_peaks()
     gbs_one = 8.0 * n / (ms_step * 1e-3) / 1e9
-    value = gbs_one * world
+    value = whole_job_gbs(8.0 * n, world, ms_step * 1e-3)
     kname = "k_sum_small" if method == xsum.XS_METHOD_SMALL else "k_sum_large"
     line = {
         "metric": METRIC,
@@ -516,7 +521,7 @@ def run_ours(args):
             "traffic": profiled_traffic(kname),
         },
         "e2e": {
-            "value": round(8.0 * n / t_e2e / 1e9 * world, 2),
+            "value": round(whole_job_gbs(8.0 * n, world, t_e2e), 2),
             "unit": "GB/s",
             "h2d_bytes_per_step": 8 * n,
             "d2h_bytes_per_step": 8,

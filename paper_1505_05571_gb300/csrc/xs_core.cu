@@ -643,7 +643,7 @@ xs_status xs_sum_async_config(const double* d_values, int64_t n, double* d_out, 
   if (method != XS_METHOD_AUTO && (block == 0 || unroll == 0)) {
     SumShape d = default_shape(ctx, n);
     if (d.method != method) d = (method == XS_METHOD_SMALL) ? SumShape{method, 128, 4}
-                                                            : SumShape{method, 256, 8};
+                                                            : SumShape{method, 256, 4};
     shape = d;
   }
   Workspace* w = workspace(ctx, s, &st);
