@@ -121,6 +121,16 @@ int xs_list_configs(int* methods, int* blocks, int* unrolls, int capacity);
  * accumulates each chunk while the next one is in flight. Blocking. */
 xs_status xs_sum_host(const double* h_values, int64_t n, double* h_out, void* stream);
 
+/* Correctly rounded exact MEAN: the exact sum divided by n, rounded once to
+ * nearest, ties to even, straight from the superaccumulator (Discussion:
+ * rounding the value of a small superaccumulator divided by a positive
+ * integer; the Introduction's motivating example is the sample mean). Unlike
+ * rounding the sum and then dividing, this is the correctly rounded mean, and
+ * it never overflows even when the sum would. Specials as for the sum; n == 0
+ * writes the default quiet NaN 0x7FF8000000000000. Asynchronous; *d_out on
+ * the device. */
+xs_status xs_mean_async(const double* d_values, int64_t n, double* d_out, void* stream);
+
 /* Inexact plain FP64 sum (a comparison baseline only, NOT exact: the rounding
  * after each addition depends on the launch shape). Writes *d_out. */
 xs_status xs_inexact_sum_async(const double* d_values, int64_t n, double* d_out, void* stream);
@@ -301,6 +311,9 @@ xs_status xs_acc_init(xs_acc h, void* stream);           /* reset to the empty s
 xs_status xs_acc_add(xs_acc h, const double* d_values, int64_t n, void* stream); /* append */
 xs_status xs_acc_merge(xs_acc dst, xs_acc src, void* stream); /* dst += src; src unchanged */
 xs_status xs_acc_round(xs_acc h, double* d_out, void* stream); /* async; state unchanged */
+/* Correctly rounded (accumulated value) / divisor, divisor >= 1 (e.g. the
+ * mean of everything appended); async; state unchanged. */
+xs_status xs_acc_round_div(xs_acc h, int64_t divisor, double* d_out, void* stream);
 xs_status xs_acc_export(xs_acc h, void* h_buf, void* stream); /* XS_ACC_BYTES, blocking */
 xs_status xs_acc_import(xs_acc h, const void* h_buf, void* stream); /* blocking */
 xs_status xs_acc_destroy(xs_acc h);

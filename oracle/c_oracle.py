@@ -40,6 +40,8 @@ def load():
         lib.xo_sum_segments_bits.restype = None
         lib.xo_sum_segments_bits.argtypes = [u64p, i64p, i64p, ctypes.c_int64, u64p]
         lib.xo_max_threads.restype = ctypes.c_int
+        lib.xo_mean_bits.restype = ctypes.c_uint64
+        lib.xo_mean_bits.argtypes = [u64p, ctypes.c_int64]
         _lib = lib
     return _lib
 
@@ -72,3 +74,9 @@ def segment_sums_bits(bits: np.ndarray, offsets: np.ndarray, seg_ids=None) -> np
 
 def max_threads() -> int:
     return int(load().xo_max_threads())
+
+
+def mean_bits(bits: np.ndarray) -> int:
+    """Bits of the correctly rounded exact mean of a uint64 (or float64) array."""
+    a = np.ascontiguousarray(bits).view(np.uint64)
+    return int(load().xo_mean_bits(_u64ptr(a), a.size))

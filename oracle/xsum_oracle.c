@@ -166,6 +166,60 @@ static uint64_t xo_finish(const xo_state *st) {
   return round_mag(A) | 0x8000000000000000ull;
 }
 
+/* Exact mean: round (P - N) / n once. The magnitude, doubled (units of
+ * 2^-1075), is divided by n from the top limb down; the quotient is rounded at
+ * the double grid with the nonzero remainder as sticky information. */
+static uint64_t round_quotient(const uint32_t *Q, int sticky_in) {
+  int top = -1;
+  for (int i = XO_LIMBS - 1; i >= 0; --i) {
+    if (Q[i]) { top = i; break; }
+  }
+  if (top < 0) return 0; /* below half of 2^-1074 */
+  int bitlen = 32 * top + (32 - __builtin_clz(Q[top]));
+  if (bitlen <= 54) { /* spacing 2^-1074 = 2 units */
+    uint64_t v = Q[0];
+    if (top >= 1) v |= (uint64_t)Q[1] << 32;
+    uint64_t m = v >> 1;
+    if ((v & 1) && (sticky_in || (m & 1))) m += 1;
+    return m;
+  }
+  int sh = bitlen - 53;
+  uint64_t m = 0;
+  for (int k = 0; k < 53; ++k) m |= (uint64_t)get_bit(Q, sh + k) << k;
+  int round = get_bit(Q, sh - 1);
+  int sticky = sticky_in || any_bit_below(Q, sh - 1);
+  if (round && (sticky || (m & 1))) m += 1;
+  if (m == (1ull << 53)) { m >>= 1; sh += 1; }
+  uint64_t e = (uint64_t)sh; /* biased exponent in units of 2^-1075 */
+  if (e >= 0x7FF) return 0x7FF0000000000000ull;
+  return ((e - 1) << 52) + m;
+}
+
+uint64_t xo_mean_bits(const uint64_t *bits, int64_t n) {
+  if (n <= 0) return 0x7FF8000000000000ull;
+  xo_state st;
+  xo_init(&st);
+  for (int64_t i = 0; i < n; ++i) xo_add(&st, bits[i]);
+  if (st.has_nan || st.pos_inf || st.neg_inf) return xo_finish(&st);
+  int c = cmp_mag(st.pos, st.neg);
+  if (c == 0) return xo_finish(&st);
+  uint32_t A[XO_LIMBS], D2[XO_LIMBS], Q[XO_LIMBS];
+  if (c > 0) sub_mag(st.pos, st.neg, A); else sub_mag(st.neg, st.pos, A);
+  /* D2 = 2 A */
+  uint32_t carry = 0;
+  for (int i = 0; i < XO_LIMBS; ++i) {
+    D2[i] = (A[i] << 1) | carry;
+    carry = A[i] >> 31;
+  }
+  unsigned __int128 rem = 0;
+  for (int i = XO_LIMBS - 1; i >= 0; --i) {
+    unsigned __int128 cur = (rem << 32) | D2[i];
+    Q[i] = (uint32_t)(cur / (uint64_t)n);
+    rem = cur % (uint64_t)n;
+  }
+  return round_quotient(Q, rem != 0) | (c < 0 ? 0x8000000000000000ull : 0);
+}
+
 uint64_t xo_sum_bits(const uint64_t *bits, int64_t n) {
   xo_state st;
   xo_init(&st);

@@ -164,6 +164,51 @@ def finish(st: ExactState) -> int:
     return round_rne(st.S)
 
 
+def round_ratio(N: int, D: int) -> int:
+    """Bits (sign excluded) of the double nearest to (N / D) * 2^-1074, ties to even.
+
+    N >= 0, D >= 1. The double grid spacing at x = N/D (in units of 2^-1074) is
+    2^k with k = max(0, bitlen(floor(x)) - 53): spacing 1 covers the subnormals
+    and the lowest normal binade. m = floor(x / 2^k) is rounded on the exact
+    remainder; a carry to 2^53 moves to the next binade.
+    """
+    if N == 0:
+        return 0
+    q = N // D
+    k = max(0, q.bit_length() - 53)
+    den = D << k
+    m, r = divmod(N, den)
+    if 2 * r > den or (2 * r == den and (m & 1)):
+        m += 1
+    if m == (1 << 53):
+        m >>= 1
+        k += 1
+    bits = (k << MANT_BITS) + m
+    return POS_INF if bits >= POS_INF else bits
+
+
+def finish_div(st: ExactState, D: int) -> int:
+    """(exact sum) / D rounded once, D >= 1; specials and signed zeros as for the sum."""
+    if st.nans or st.pos_inf or st.neg_inf or st.S == 0:
+        return finish(st)
+    sign = SIGN_BIT if st.S < 0 else 0
+    return round_ratio(abs(st.S), D) | sign
+
+
+def finish_mean(st: ExactState) -> int:
+    """Correctly rounded exact mean: (exact sum) / n rounded once (Discussion).
+
+    n = 0 gives the default quiet NaN (0/0).
+    """
+    if st.n == 0:
+        return DEFAULT_NAN
+    return finish_div(st, st.n)
+
+
+def mean_bits(bits) -> int:
+    return finish_mean(state_of_bits(bits))
+
+
 def state_of_bits(bits) -> ExactState:
     st = ExactState()
     for b in bits:

@@ -29,6 +29,7 @@ struct SumArgs {
   int mode;        // 0: round into out and reset g; 1: normalise g in place
   int carry_tiles; // small kernel: tiles between per-thread carry propagations
   int prefetch;    // tiles of this block prefetched into L2 ahead of use (0 = off)
+  unsigned long long divisor;  // mode 0: 0 rounds the sum, d >= 1 rounds the sum / d
 };
 
 // Ticket epilogue: the last block to arrive finishes the sum.
@@ -55,7 +56,8 @@ __device__ void finish_grid(const SumArgs& a) {
     }
     flags = __shfl_sync(kFull, flags, 0);
     key = __shfl_sync(kFull, key, 0);
-    const unsigned long long bits = warp_round(v0, v1, v2, flags, key);
+    const unsigned long long bits = a.divisor ? warp_round_div(v0, v1, v2, flags, key, a.divisor)
+                                              : warp_round(v0, v1, v2, flags, key);
     if (lane == 0) *reinterpret_cast<unsigned long long*>(a.out) = bits;
   } else {
     long long v0 = (long long)__ldcg(ch + lane);
@@ -290,13 +292,15 @@ __global__ void k_acc_merge(AccState* dst, const AccState* src) {
   }
 }
 
-// Rounded value of an accumulator; the state is left unchanged. One warp.
-__global__ void k_acc_round(const AccState* s, double* out) {
+// Rounded value of an accumulator, or of its value divided by d >= 1; the
+// state is left unchanged. One warp.
+__global__ void k_acc_round(const AccState* s, double* out, unsigned long long d) {
   const int lane = threadIdx.x;
   const long long v0 = s->chunk[lane];
   const long long v1 = s->chunk[lane + 32];
   const long long v2 = lane < 3 ? s->chunk[lane + 64] : 0;
-  const unsigned long long bits = warp_round(v0, v1, v2, s->flags, s->nan_key);
+  const unsigned long long bits = d ? warp_round_div(v0, v1, v2, s->flags, s->nan_key, d)
+                                    : warp_round(v0, v1, v2, s->flags, s->nan_key);
   if (lane == 0) *reinterpret_cast<unsigned long long*>(out) = bits;
 }
 
@@ -507,7 +511,8 @@ SumShape default_shape(DeviceCtx* ctx, int64_t n) {
 }
 
 xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState* target,
-                     double* d_out, int mode, SumShape shape, int grid, cudaStream_t s) {
+                     double* d_out, int mode, SumShape shape, int grid, cudaStream_t s,
+                     unsigned long long divisor) {
   const int k = find_kernel(shape.method, shape.block, shape.unroll);
   if (k < 0) return set_error(XS_ERR_NOT_SUPPORTED);
   const KernelEntry& K = kKernels[k];
@@ -524,6 +529,7 @@ xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState
   a.mode = mode;
   a.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * K.unroll));
   a.prefetch = g_prefetch_tiles;
+  a.divisor = divisor;
   K.fn<<<(unsigned)g, K.block, K.smem, s>>>(a);
   XS_TRY_CUDA(cudaGetLastError());
   return XS_OK;
@@ -546,6 +552,7 @@ xs_status launch_small_fixed(const double* d_values, int64_t n, AccState* target
   a.mode = 0;
   a.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * U));
   a.prefetch = g_prefetch_tiles;
+  a.divisor = 0ull;
   k_sum_small<B, U><<<(unsigned)g, B, small_smem<B>(), s>>>(a);
   XS_TRY_CUDA(cudaGetLastError());
   return XS_OK;
@@ -733,7 +740,7 @@ xs_status xs_sum_host(const double* h_values, int64_t n, double* h_out, void* st
     XS_TRY_CUDA(cudaEventRecord(w->free_[slot], s));
     done += m;
   }
-  k_acc_round<<<1, 32, 0, s>>>(w->acc_host, w->d_out);
+  k_acc_round<<<1, 32, 0, s>>>(w->acc_host, w->d_out, 0ull);
   XS_TRY_CUDA(cudaGetLastError());
   XS_TRY_CUDA(cudaMemcpyAsync(w->h_out, w->d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
   XS_TRY_CUDA(cudaStreamSynchronize(s));
@@ -819,6 +826,28 @@ xs_status xs_autotune_sum(const double* d_values, int64_t n, int reps, void* str
   return set_error(XS_OK);
 }
 
+xs_status xs_mean_async(const double* d_values, int64_t n, double* d_out, void* stream) {
+  xs_status st = check_values(d_values, n);
+  if (st != XS_OK) return st;
+  if ((st = check_device_ptr(d_out)) != XS_OK) return st;
+  if (((uintptr_t)d_out & 7u) != 0u) return set_error(XS_ERR_INVALID_VALUE);
+  cudaStream_t s = as_stream(stream);
+  if (n == 0) {  // 0 / 0
+    static const unsigned long long kNaNBits = 0x7FF8000000000000ull;
+    XS_TRY_CUDA(cudaMemcpyAsync(d_out, &kNaNBits, sizeof(double), cudaMemcpyHostToDevice, s));
+    XS_TRY_CUDA(cudaStreamSynchronize(s));
+    return set_error(XS_OK);
+  }
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  Workspace* w = workspace(ctx, s, &st);
+  if (!w) return st;
+  st = launch_sum(ctx, d_values, n, w->acc, d_out, 0, default_shape(ctx, n), 0, s,
+                  (unsigned long long)n);
+  if (st != XS_OK) return st;
+  return set_error(XS_OK);
+}
+
 // ----------------------------- accumulator handles --------------------------
 
 struct xs_acc_s {
@@ -879,7 +908,17 @@ xs_status xs_acc_round(xs_acc h, double* d_out, void* stream) {
   if (h == nullptr) return set_error(XS_ERR_INVALID_POINTER);
   xs_status st = check_device_ptr(d_out);
   if (st != XS_OK) return st;
-  k_acc_round<<<1, 32, 0, as_stream(stream)>>>(h->d, d_out);
+  k_acc_round<<<1, 32, 0, as_stream(stream)>>>(h->d, d_out, 0ull);
+  XS_TRY_CUDA(cudaGetLastError());
+  return set_error(XS_OK);
+}
+
+xs_status xs_acc_round_div(xs_acc h, int64_t divisor, double* d_out, void* stream) {
+  if (h == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  if (divisor < 1) return set_error(XS_ERR_INVALID_VALUE);
+  xs_status st = check_device_ptr(d_out);
+  if (st != XS_OK) return st;
+  k_acc_round<<<1, 32, 0, as_stream(stream)>>>(h->d, d_out, (unsigned long long)divisor);
   XS_TRY_CUDA(cudaGetLastError());
   return set_error(XS_OK);
 }

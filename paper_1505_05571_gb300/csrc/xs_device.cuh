@@ -362,16 +362,8 @@ __device__ __forceinline__ unsigned lanes_below(int x) {
   return x <= 0 ? 0u : (x >= 32 ? kFull : ((1u << x) - 1u));
 }
 
-// Correct rounding, ties to even (small-superaccumulator section on
-// rounding; overflow as in the Discussion). All 32 lanes call it; the
-// returned bit pattern is valid in every lane.
-__device__ __noinline__ static unsigned long long warp_round(long long v0, long long v1, long long v2,
-                                         unsigned flags, unsigned long long nan_key) {
-  if (nan_key != 0ull) return nan_from_key(nan_key);
-  if ((flags & (kFlagPosInf | kFlagNegInf)) == (kFlagPosInf | kFlagNegInf)) return kDefaultNaN;
-  if (flags & kFlagPosInf) return kPosInf;
-  if (flags & kFlagNegInf) return kNegInf;
-  const int lane = threadIdx.x & 31;
+// Normalise and take the magnitude; returns whether the value is negative.
+__device__ __forceinline__ bool warp_abs(long long& v0, long long& v1, long long& v2) {
   warp_normalize(v0, v1, v2);
   const bool neg = __shfl_sync(kFull, v2, 2) < 0;
   if (neg) {
@@ -380,12 +372,19 @@ __device__ __noinline__ static unsigned long long warp_round(long long v0, long 
     v2 = -v2;
     warp_normalize(v0, v1, v2);
   }
+  return neg;
+}
+
+// Round to nearest, ties to even, the magnitude A * 2^-1075 + (something in
+// (0, 2^-1075) when sticky_in), A given as normalised non-negative chunks
+// (small section on rounding; overflow as in the Discussion). All 32 lanes
+// call it; the result (without sign) is valid in every lane.
+__device__ __noinline__ static unsigned long long warp_round_mag(long long v0, long long v1,
+                                                                 long long v2, bool sticky_in) {
   const unsigned b0 = __ballot_sync(kFull, v0 != 0);
   const unsigned b1 = __ballot_sync(kFull, v1 != 0);
   const unsigned b2 = __ballot_sync(kFull, v2 != 0);
-  if ((b0 | b1 | b2) == 0u) {
-    return ((flags & kFlagAny) && !(flags & kFlagNotNegZero)) ? kNegZero : 0ull;
-  }
+  if ((b0 | b1 | b2) == 0u) return 0ull;  // below half of 2^-1074: rounds to zero
   const int h = b2 ? 64 + 31 - __clz(b2) : (b1 ? 32 + 31 - __clz(b1) : 31 - __clz(b0));
   auto chunk_at = [&](int k) -> unsigned long long {
     const int slot = k < 0 ? 0 : (k >> 5);
@@ -399,27 +398,100 @@ __device__ __noinline__ static unsigned long long warp_round(long long v0, long 
   const int below = h - 2;
   const bool sticky_low = ((b0 & lanes_below(below)) | (b1 & lanes_below(below - 32)) |
                            (b2 & lanes_below(below - 64))) != 0u;
-  (void)lane;
-  unsigned long long bits;
   const int tb = 63 - __clzll((long long)dh);  // top bit of chunk h
-  const int P = 32 * h + tb;                   // top bit of the magnitude, units 2^-1075
+  const int P = 32 * h + tb;                   // top bit of A
+  unsigned long long bits;
   if (P < 54) {
-    // |sum| < 2^53 units of 2^-1074: exact, and its pattern is the integer itself.
+    // below 2^-1021: the last kept bit is 2^-1074 (bit 1 of A); the pattern of
+    // a subnormal or lowest-binade double is its integer multiple of 2^-1074
     const unsigned long long A = (h >= 1 ? (chunk_at(1) << 32) : 0ull) + chunk_at(0);
     bits = A >> 1;
+    if ((A & 1ull) && (sticky_in || (bits & 1ull))) bits += 1ull;
   } else {
     const unsigned __int128 W = ((unsigned __int128)dh << 64) | ((unsigned __int128)dm << 32) |
                                 (unsigned __int128)dl;
     unsigned long long q = (unsigned long long)(W >> (tb + 12));  // 53 bits
     const bool rbit = (unsigned)(W >> (tb + 11)) & 1u;
     const unsigned __int128 rest_mask = (((unsigned __int128)1) << (tb + 11)) - 1;
-    const bool sticky = sticky_low || ((W & rest_mask) != 0);
+    const bool sticky = sticky_in || sticky_low || ((W & rest_mask) != 0);
     if (rbit && (sticky || (q & 1ull))) q += 1ull;
     const unsigned long long e = (unsigned long long)(P - 52);  // biased exponent
     bits = ((e - 1ull) << 52) + q;  // a carry out of q bumps the exponent
     if (bits >= kPosInf) bits = kPosInf;
   }
-  return bits | (neg ? kNegZero : 0ull);
+  return bits;
+}
+
+// Special values first (Inf/NaN record of Fig. 3, readings of the method).
+__device__ __forceinline__ bool special_result(unsigned flags, unsigned long long nan_key,
+                                               unsigned long long* out) {
+  if (nan_key != 0ull) { *out = nan_from_key(nan_key); return true; }
+  if ((flags & (kFlagPosInf | kFlagNegInf)) == (kFlagPosInf | kFlagNegInf)) {
+    *out = kDefaultNaN;
+    return true;
+  }
+  if (flags & kFlagPosInf) { *out = kPosInf; return true; }
+  if (flags & kFlagNegInf) { *out = kNegInf; return true; }
+  return false;
+}
+
+__device__ __forceinline__ bool warp_is_zero(long long v0, long long v1, long long v2) {
+  return !__any_sync(kFull, (v0 | v1 | v2) != 0);
+}
+
+__device__ __forceinline__ unsigned long long signed_zero(unsigned flags) {
+  return ((flags & kFlagAny) && !(flags & kFlagNotNegZero)) ? kNegZero : 0ull;
+}
+
+// Correctly rounded exact sum (ties to even) of an accumulator whose chunks
+// are spread over the warp as above.
+__device__ __noinline__ static unsigned long long warp_round(long long v0, long long v1,
+                                                             long long v2, unsigned flags,
+                                                             unsigned long long nan_key) {
+  unsigned long long sp;
+  if (special_result(flags, nan_key, &sp)) return sp;
+  const bool neg = warp_abs(v0, v1, v2);
+  if (warp_is_zero(v0, v1, v2)) return signed_zero(flags);
+  return warp_round_mag(v0, v1, v2, false) | (neg ? kNegZero : 0ull);
+}
+
+// Long division of the normalised magnitude by d >= 1, from the top chunk
+// down; every lane runs the same recurrence (rem < d, so each quotient chunk
+// of 0..65 is below 2^32). Returns whether the remainder is nonzero.
+__device__ __noinline__ static bool warp_divide(long long& v0, long long& v1, long long& v2,
+                                                unsigned long long d) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long rem = 0ull;
+  for (int k = kSChunks - 1; k >= 0; --k) {
+    const int slot = k >> 5;
+    const long long sv = slot == 0 ? v0 : (slot == 1 ? v1 : v2);
+    const unsigned long long limb = (unsigned long long)__shfl_sync(kFull, sv, k & 31);
+    const unsigned __int128 cur = ((unsigned __int128)rem << 32) + limb;
+    const unsigned __int128 q = cur / d;
+    rem = (unsigned long long)(cur - q * d);
+    if ((k & 31) == lane) {
+      if (slot == 0) v0 = (long long)q;
+      else if (slot == 1) v1 = (long long)q;
+      else v2 = (long long)q;
+    }
+  }
+  return rem != 0ull;
+}
+
+// Correctly rounded quotient (exact sum) / d, ties to even -- the exact mean
+// when d is the number of terms (Discussion: rounding the superaccumulator
+// divided by a positive integer directly). The quotient of a finite sum never
+// exceeds the largest term in magnitude, so it cannot overflow.
+__device__ __noinline__ static unsigned long long warp_round_div(long long v0, long long v1,
+                                                                 long long v2, unsigned flags,
+                                                                 unsigned long long nan_key,
+                                                                 unsigned long long d) {
+  unsigned long long sp;
+  if (special_result(flags, nan_key, &sp)) return sp;
+  const bool neg = warp_abs(v0, v1, v2);
+  if (warp_is_zero(v0, v1, v2)) return signed_zero(flags);
+  const bool sticky = warp_divide(v0, v1, v2, d);
+  return warp_round_mag(v0, v1, v2, sticky) | (neg ? kNegZero : 0ull);
 }
 
 // --------------------------------------------------------------------------

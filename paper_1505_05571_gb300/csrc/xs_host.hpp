@@ -68,7 +68,8 @@ Workspace* workspace(DeviceCtx* ctx, cudaStream_t s, xs_status* st);
 // mode 0: round into d_out and reset the target; mode 1: normalise the target
 // in place (accumulator handles).
 xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState* target,
-                     double* d_out, int mode, SumShape shape, int grid, cudaStream_t s);
+                     double* d_out, int mode, SumShape shape, int grid, cudaStream_t s,
+                     unsigned long long divisor = 0);
 SumShape default_shape(DeviceCtx* ctx, int64_t n);
 xs_status launch_small_fixed(const double* d_values, int64_t n, AccState* target, double* d_out,
                              int grid, cudaStream_t s);

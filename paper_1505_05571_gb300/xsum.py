@@ -93,6 +93,8 @@ _SIGS = {
     "xs_sum_host": (ctypes.c_int, [_vp, _c_int64, ctypes.POINTER(ctypes.c_double), _vp]),
     "xs_sum_noalloc": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_inexact_sum_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
+    "xs_mean_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
+    "xs_acc_round_div": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_autotune_sum": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
@@ -249,6 +251,14 @@ XS_NOALLOC_MAX_TERMS = 1 << 45
 def xs_sum_noalloc(d_values, n: int, d_out, stream=None) -> None:
     _check(load().xs_sum_noalloc(_ptr(d_values), n, _ptr(d_out), _stream(stream)),
            "xs_sum_noalloc")
+
+
+def xs_mean_async(d_values, n: int, d_out, stream=None) -> None:
+    _check(load().xs_mean_async(_ptr(d_values), n, _ptr(d_out), _stream(stream)), "xs_mean_async")
+
+
+def xs_acc_round_div(h: int, divisor: int, d_out, stream=None) -> None:
+    _check(load().xs_acc_round_div(h, divisor, _ptr(d_out), _stream(stream)), "xs_acc_round_div")
 
 
 def xs_inexact_sum_async(d_values, n: int, d_out, stream=None) -> None:
