@@ -46,9 +46,12 @@ def read_peaks():
 # Source regions that define each profiled kernel: the shared device header
 # plus the kernel's own section of its translation unit.
 KERNEL_SOURCES = {
-    "k_sum_small": ("xs_core.cu", "struct SumArgs {", "// Large superaccumulator kernel"),
-    "k_sum_large": ("xs_core.cu", "// Large superaccumulator kernel", "// Accumulator-handle kernels"),
-    "k_seg_main": ("xs_segments.cu", "struct SegArgs {", "namespace {"),
+    "k_sum_small": [("xs_kernels.cuh", None, None),
+                    ("xs_core.cu", "__device__ __forceinline__ void load_tile(",
+                     "// Large superaccumulator kernel")],
+    "k_sum_large": [("xs_kernels.cuh", None, None),
+                    ("xs_core.cu", "// Large superaccumulator kernel", "// Accumulator-handle kernels")],
+    "k_seg_main": [("xs_segments.cu", "struct SegArgs {", "namespace {")],
 }
 
 
@@ -58,11 +61,14 @@ def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     with open(os.path.join(csrc, "xs_device.cuh"), "rb") as fh:
         h.update(fh.read())
-    f, start, end = KERNEL_SOURCES[kernel]
-    with open(os.path.join(csrc, f)) as fh:
-        text = fh.read()
-    i = text.index(start)
-    h.update(text[i:text.index(end, i + len(start))].encode())
+    for f, start, end in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(csrc, f)) as fh:
+            text = fh.read()
+        if start is None:
+            h.update(text.encode())
+            continue
+        i = text.index(start)
+        h.update(text[i:text.index(end, i + len(start))].encode())
     return h.hexdigest()[:16]
 
 

@@ -131,6 +131,27 @@ xs_status xs_sum_host(const double* h_values, int64_t n, double* h_out, void* st
  * the device. */
 xs_status xs_mean_async(const double* d_values, int64_t n, double* d_out, void* stream);
 
+/* Exact dot product: each product d_x[i] * d_y[i] is rounded to the nearest
+ * double (IEEE multiply), the n products are summed exactly and the sum is
+ * rounded once (performance section: squared norm and dot product computed
+ * with the superaccumulator summation). Reading: a NaN product (NaN input, or
+ * Inf times 0) counts as the default quiet NaN 0x7FF8000000000000. The two
+ * vectors may have different 16-byte alignment. Asynchronous; *d_out on the
+ * device. */
+xs_status xs_dot_async(const double* d_x, const double* d_y, int64_t n, double* d_out,
+                       void* stream);
+/* Exact squared norm: the sum of the rounded squares d_x[i] * d_x[i], rounded
+ * once (same passage). */
+xs_status xs_norm2_async(const double* d_x, int64_t n, double* d_out, void* stream);
+
+/* Exact sum of binary32 values, rounded once to the nearest float, ties to
+ * even -- the single-precision variant with a smaller superaccumulator
+ * (Introduction). Same result rules as the double sum, with float constants:
+ * largest 22-bit NaN payload, default NaN 0x7FC00000, overflow when
+ * |sum| >= 2^128 - 2^103. d_values 4-byte aligned; *d_out is a device float;
+ * n <= 2^39 (XS_ERR_INVALID_VALUE above). Asynchronous. */
+xs_status xs_sum_f32_async(const float* d_values, int64_t n, float* d_out, void* stream);
+
 /* Inexact plain FP64 sum (a comparison baseline only, NOT exact: the rounding
  * after each addition depends on the launch shape). Writes *d_out. */
 xs_status xs_inexact_sum_async(const double* d_values, int64_t n, double* d_out, void* stream);

@@ -40,6 +40,8 @@ def load():
         lib.xo_sum_segments_bits.restype = None
         lib.xo_sum_segments_bits.argtypes = [u64p, i64p, i64p, ctypes.c_int64, u64p]
         lib.xo_max_threads.restype = ctypes.c_int
+        lib.xo_sum_f32_bits.restype = ctypes.c_uint32
+        lib.xo_sum_f32_bits.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64]
         lib.xo_mean_bits.restype = ctypes.c_uint64
         lib.xo_mean_bits.argtypes = [u64p, ctypes.c_int64]
         _lib = lib
@@ -80,3 +82,9 @@ def mean_bits(bits: np.ndarray) -> int:
     """Bits of the correctly rounded exact mean of a uint64 (or float64) array."""
     a = np.ascontiguousarray(bits).view(np.uint64)
     return int(load().xo_mean_bits(_u64ptr(a), a.size))
+
+
+def sum_f32_bits(bits32: np.ndarray) -> int:
+    """Bits of the correctly rounded exact float sum of a uint32 (or float32) array."""
+    a = np.ascontiguousarray(bits32).view(np.uint32)
+    return int(load().xo_sum_f32_bits(a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), a.size))

@@ -220,6 +220,67 @@ uint64_t xo_mean_bits(const uint64_t *bits, int64_t n) {
   return round_quotient(Q, rem != 0) | (c < 0 ? 0x8000000000000000ull : 0);
 }
 
+/* Single precision: terms K = M << (e_eff - 1) in units of 2^-149, same
+ * two-magnitude sum, rounded to a 24-bit significand. */
+static uint32_t round_mag32(const uint32_t *A) {
+  int top = -1;
+  for (int i = XO_LIMBS - 1; i >= 0; --i) {
+    if (A[i]) { top = i; break; }
+  }
+  if (top < 0) return 0;
+  int bitlen = 32 * top + (32 - __builtin_clz(A[top]));
+  if (bitlen <= 24) return A[0];
+  int sh = bitlen - 24;
+  uint32_t q = 0;
+  for (int k = 0; k < 24; ++k) q |= (uint32_t)get_bit(A, sh + k) << k;
+  int round = get_bit(A, sh - 1);
+  int sticky = any_bit_below(A, sh - 1);
+  if (round && (sticky || (q & 1))) q += 1;
+  if (q == (1u << 24)) { q >>= 1; sh += 1; }
+  uint32_t e = (uint32_t)sh + 1;
+  if (e >= 0xFF) return 0x7F800000u;
+  return ((e - 1) << 23) + q;
+}
+
+uint32_t xo_sum_f32_bits(const uint32_t *bits, int64_t n) {
+  uint32_t P[XO_LIMBS], N[XO_LIMBS];
+  memset(P, 0, sizeof P);
+  memset(N, 0, sizeof N);
+  int pinf = 0, ninf = 0, has_nan = 0, allneg = 1;
+  uint32_t nanb = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t b = bits[i];
+    if (b != 0x80000000u) allneg = 0;
+    uint32_t s = b >> 31, e = (b >> 23) & 0xFF, m = b & 0x7FFFFF;
+    if (e == 0xFF) {
+      if (m == 0) {
+        if (s) ninf = 1; else pinf = 1;
+      } else {
+        const uint32_t pl = b & 0x3FFFFF, cur = nanb & 0x3FFFFF;
+        if (!has_nan || pl > cur || (pl == cur && b < nanb)) nanb = b;
+        has_nan = 1;
+      }
+      continue;
+    }
+    if (e == 0 && m == 0) continue;
+    uint64_t M = e == 0 ? m : (m | (1u << 23));
+    add_shifted(s ? N : P, M, e == 0 ? 0 : (int)e - 1);
+  }
+  if (has_nan) return nanb | 0x400000u;
+  if (pinf && ninf) return 0x7FC00000u;
+  if (pinf) return 0x7F800000u;
+  if (ninf) return 0xFF800000u;
+  int c = cmp_mag(P, N);
+  if (c == 0) return (n > 0 && allneg) ? 0x80000000u : 0u;
+  uint32_t A[XO_LIMBS];
+  if (c > 0) {
+    sub_mag(P, N, A);
+    return round_mag32(A);
+  }
+  sub_mag(N, P, A);
+  return round_mag32(A) | 0x80000000u;
+}
+
 uint64_t xo_sum_bits(const uint64_t *bits, int64_t n) {
   xo_state st;
   xo_init(&st);

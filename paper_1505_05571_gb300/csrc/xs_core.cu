@@ -18,85 +18,9 @@
 #include <vector>
 
 #include "xs_host.hpp"
+#include "xs_kernels.cuh"
 
 namespace xs {
-
-struct SumArgs {
-  const double* x;
-  long long n;
-  AccState* g;     // global accumulator: zeroed workspace, or a handle's state
-  double* out;     // mode 0: result
-  int mode;        // 0: round into out and reset g; 1: normalise g in place
-  int carry_tiles; // small kernel: tiles between per-thread carry propagations
-  int prefetch;    // tiles of this block prefetched into L2 ahead of use (0 = off)
-  unsigned long long divisor;  // mode 0: 0 rounds the sum, d >= 1 rounds the sum / d
-};
-
-// Ticket epilogue: the last block to arrive finishes the sum.
-__device__ void finish_grid(const SumArgs& a) {
-  __shared__ unsigned s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(&a.g->ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
-  __syncthreads();
-  if (!s_last || threadIdx.x >= 32) return;
-  __threadfence();
-  const int lane = threadIdx.x;
-  unsigned long long* ch = reinterpret_cast<unsigned long long*>(a.g->chunk);
-  if (a.mode == 0) {
-    long long v0 = (long long)atomicExch(ch + lane, 0ull);
-    long long v1 = (long long)atomicExch(ch + lane + 32, 0ull);
-    long long v2 = lane < 3 ? (long long)atomicExch(ch + lane + 64, 0ull) : 0;
-    unsigned flags = 0u;
-    unsigned long long key = 0ull;
-    if (lane == 0) {
-      flags = atomicExch(&a.g->flags, 0u);
-      key = atomicExch(&a.g->nan_key, 0ull);
-      atomicExch(&a.g->ticket, 0u);
-    }
-    flags = __shfl_sync(kFull, flags, 0);
-    key = __shfl_sync(kFull, key, 0);
-    const unsigned long long bits = a.divisor ? warp_round_div(v0, v1, v2, flags, key, a.divisor)
-                                              : warp_round(v0, v1, v2, flags, key);
-    if (lane == 0) *reinterpret_cast<unsigned long long*>(a.out) = bits;
-  } else {
-    long long v0 = (long long)__ldcg(ch + lane);
-    long long v1 = (long long)__ldcg(ch + lane + 32);
-    long long v2 = lane < 3 ? (long long)__ldcg(ch + lane + 64) : 0;
-    warp_normalize(v0, v1, v2);
-    ch[lane] = (unsigned long long)v0;
-    ch[lane + 32] = (unsigned long long)v1;
-    if (lane < 3) ch[lane + 64] = (unsigned long long)v2;
-    if (lane == 0) a.g->ticket = 0u;
-  }
-}
-
-// Split of the input into an optional unaligned head element, 16-byte pairs
-// and an optional tail element.
-struct Split {
-  int head;
-  bool tail;
-  long long npairs;
-  const ulonglong2* xv;
-};
-__device__ __forceinline__ Split split_input(const double* x, long long n) {
-  Split s;
-  s.head = (((uintptr_t)x & 15u) != 0u && n > 0) ? 1 : 0;
-  const long long body = n - s.head;
-  s.npairs = body >> 1;
-  s.tail = (body & 1) != 0;
-  s.xv = reinterpret_cast<const ulonglong2*>(x + s.head);
-  return s;
-}
-
-// L2 prefetch of tile t (clamped to the input).
-template <int BLOCK, int UNROLL>
-__device__ __forceinline__ void prefetch_tile(const Split& sp, long long t, long long ntiles) {
-  if (t >= ntiles) return;
-  const long long first = t * (long long)(BLOCK * UNROLL);
-  const long long cnt = min((long long)(BLOCK * UNROLL), sp.npairs - first);
-  prefetch_l2(sp.xv + first, (unsigned)(cnt * 16));
-}
 
 template <int BLOCK, int UNROLL>
 __device__ __forceinline__ void load_tile(const Split& sp, long long t, int tid, ulonglong2* buf) {
@@ -112,22 +36,6 @@ __device__ __forceinline__ void load_tile(const Split& sp, long long t, int tid,
 // ---------------------------------------------------------------------------
 // Small superaccumulator kernel
 // ---------------------------------------------------------------------------
-
-// Block partial -> global accumulator, plus the special-value record.
-template <int BLOCK>
-__device__ __forceinline__ void block_small_to_global(const long long* sm, const SumArgs& a,
-                                                      unsigned flags, unsigned long long nkey) {
-  unsigned long long* g = reinterpret_cast<unsigned long long*>(a.g->chunk);
-  block_chunk_sums<BLOCK>(sm, [&](int c, long long v) {
-    if (v != 0) atomicAdd(g + c, (unsigned long long)v);
-  });
-  flags = __reduce_or_sync(kFull, flags);
-  nkey = warp_max_ull(nkey);
-  if ((threadIdx.x & 31) == 0) {
-    if (flags) atomicOr(&a.g->flags, flags);
-    if (nkey) atomicMax(&a.g->nan_key, nkey);
-  }
-}
 
 // Full tile t: no bounds checks.
 template <int BLOCK, int UNROLL>
@@ -484,11 +392,12 @@ Workspace* workspace(DeviceCtx* ctx, cudaStream_t s, xs_status* st) {
     return it->second;
   }
   Workspace* w = new Workspace();
-  cudaError_t e = cudaMalloc(&w->acc, 2 * sizeof(AccState) + 64);
-  if (e == cudaSuccess) e = cudaMemset(w->acc, 0, 2 * sizeof(AccState) + 64);
+  cudaError_t e = cudaMalloc(&w->acc, 3 * sizeof(AccState) + 64);
+  if (e == cudaSuccess) e = cudaMemset(w->acc, 0, 3 * sizeof(AccState) + 64);
   if (e == cudaSuccess) {
     w->acc_host = w->acc + 1;
-    w->d_out = reinterpret_cast<double*>(w->acc + 2);
+    w->acc_f32 = w->acc + 2;
+    w->d_out = reinterpret_cast<double*>(w->acc + 3);
     e = cudaMallocHost(&w->h_out, sizeof(double));
   }
   if (e != cudaSuccess) {

@@ -455,20 +455,53 @@ __device__ __noinline__ static unsigned long long warp_round(long long v0, long 
   return warp_round_mag(v0, v1, v2, false) | (neg ? kNegZero : 0ull);
 }
 
-// Long division of the normalised magnitude by d >= 1, from the top chunk
-// down; every lane runs the same recurrence (rem < d, so each quotient chunk
-// of 0..65 is below 2^32). Returns whether the remainder is nonzero.
+// Long division of the normalised magnitude by d >= 1, from its top nonzero
+// chunk down; every lane runs the same recurrence. Each step divides
+// cur = rem * 2^32 + chunk (rem < d) by d: a double-precision estimate of the
+// quotient is within one of the truth, and exact integer corrections fix it.
+// Returns whether the remainder is nonzero.
 __device__ __noinline__ static bool warp_divide(long long& v0, long long& v1, long long& v2,
                                                 unsigned long long d) {
   const int lane = threadIdx.x & 31;
+  const unsigned b0 = __ballot_sync(kFull, v0 != 0);
+  const unsigned b1 = __ballot_sync(kFull, v1 != 0);
+  const unsigned b2 = __ballot_sync(kFull, v2 != 0);
+  if ((b0 | b1 | b2) == 0u) return false;
+  const int h = b2 ? 64 + 31 - __clz(b2) : (b1 ? 32 + 31 - __clz(b1) : 31 - __clz(b0));
   unsigned long long rem = 0ull;
-  for (int k = kSChunks - 1; k >= 0; --k) {
+  if (d <= 0xFFFFFFFFull) {
+    // cur = rem * 2^32 + chunk < 2^64 (for the top chunk, chunk < 2^34 and
+    // rem = 0); q from the integer reciprocal m = floor((2^64 - 1) / d) is at
+    // most two below the truth
+    const unsigned long long m = 0xFFFFFFFFFFFFFFFFull / d;
+    for (int k = h; k >= 0; --k) {
+      const int slot = k >> 5;
+      const long long sv = slot == 0 ? v0 : (slot == 1 ? v1 : v2);
+      const unsigned long long limb = (unsigned long long)__shfl_sync(kFull, sv, k & 31);
+      const unsigned long long cur = (rem << 32) + limb;
+      unsigned long long q = __umul64hi(cur, m);
+      unsigned long long r = cur - q * d;
+      for (int fix = 0; fix < 4 && r >= d; ++fix) { ++q; r -= d; }
+      rem = r;
+      if ((k & 31) == lane) {
+        if (slot == 0) v0 = (long long)q;
+        else if (slot == 1) v1 = (long long)q;
+        else v2 = (long long)q;
+      }
+    }
+    return rem != 0ull;
+  }
+  const double inv = 1.0 / (double)d;
+  for (int k = h; k >= 0; --k) {
     const int slot = k >> 5;
     const long long sv = slot == 0 ? v0 : (slot == 1 ? v1 : v2);
     const unsigned long long limb = (unsigned long long)__shfl_sync(kFull, sv, k & 31);
-    const unsigned __int128 cur = ((unsigned __int128)rem << 32) + limb;
-    const unsigned __int128 q = cur / d;
-    rem = (unsigned long long)(cur - q * d);
+    const double est = __fma_rn((double)rem, 4294967296.0, (double)limb) * inv;
+    unsigned long long q = est > 0.0 ? (unsigned long long)est : 0ull;
+    __int128 r = (((__int128)rem) << 32) + (__int128)limb - (__int128)q * (__int128)d;
+    for (int fix = 0; fix < 4 && r < 0; ++fix) { --q; r += d; }
+    for (int fix = 0; fix < 4 && r >= (__int128)d; ++fix) { ++q; r -= d; }
+    rem = (unsigned long long)r;
     if ((k & 31) == lane) {
       if (slot == 0) v0 = (long long)q;
       else if (slot == 1) v1 = (long long)q;

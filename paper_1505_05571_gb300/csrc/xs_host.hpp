@@ -32,6 +32,7 @@ xs_status check_device_ptr(const void* p);
 struct Workspace {
   AccState* acc = nullptr;        // grid accumulator of xs_sum
   AccState* acc_host = nullptr;   // accumulator of xs_sum_host
+  AccState* acc_f32 = nullptr;    // grid accumulator of the FP32 sum (its smaller layout)
   double* d_out = nullptr;        // device result slot
   double* h_out = nullptr;        // pinned result slot
   // xs_sum_host staging ring

@@ -94,6 +94,9 @@ _SIGS = {
     "xs_sum_noalloc": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_inexact_sum_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_mean_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
+    "xs_dot_async": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, _vp]),
+    "xs_norm2_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
+    "xs_sum_f32_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_acc_round_div": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_autotune_sum": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -255,6 +258,20 @@ def xs_sum_noalloc(d_values, n: int, d_out, stream=None) -> None:
 
 def xs_mean_async(d_values, n: int, d_out, stream=None) -> None:
     _check(load().xs_mean_async(_ptr(d_values), n, _ptr(d_out), _stream(stream)), "xs_mean_async")
+
+
+def xs_dot_async(d_x, d_y, n: int, d_out, stream=None) -> None:
+    _check(load().xs_dot_async(_ptr(d_x), _ptr(d_y), n, _ptr(d_out), _stream(stream)),
+           "xs_dot_async")
+
+
+def xs_norm2_async(d_x, n: int, d_out, stream=None) -> None:
+    _check(load().xs_norm2_async(_ptr(d_x), n, _ptr(d_out), _stream(stream)), "xs_norm2_async")
+
+
+def xs_sum_f32_async(d_values, n: int, d_out, stream=None) -> None:
+    _check(load().xs_sum_f32_async(_ptr(d_values), n, _ptr(d_out), _stream(stream)),
+           "xs_sum_f32_async")
 
 
 def xs_acc_round_div(h: int, divisor: int, d_out, stream=None) -> None:

@@ -1,0 +1,48 @@
+"""GPU parity of the binary32 exact sum against the oracle (bit for bit)."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import c_oracle
+from tests.test_oracle32 import GOLDEN32, rand32
+from paper_1505_05571_gb300 import xsum
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu32(bits, misalign=0):
+    a = np.ascontiguousarray(bits, dtype=np.uint32).view(np.int32)
+    t = torch.empty(a.size + misalign, dtype=torch.int32, device="cuda")
+    if a.size:
+        t[misalign:].copy_(torch.from_numpy(a))
+    d = t[misalign:].view(torch.float32)
+    out = torch.full((1,), float("nan"), dtype=torch.float32, device="cuda")
+    xsum.xs_sum_f32_async(d, d.numel(), out)
+    return int(out.view(torch.int32).cpu().numpy().view(np.uint32)[0])
+
+
+@pytest.mark.parametrize("bits,expected,why", GOLDEN32)
+def test_golden(bits, expected, why):
+    for mis in range(4):
+        assert gpu32(np.array(bits, dtype=np.uint32), mis) == expected
+
+
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 7, 2049, 65536 + 3, 3_000_001])
+def test_sizes_and_alignments(n):
+    for x in (rand32(n, n), rand32(n + 1, n, -30, 30), rand32(n + 2, n, -149, -120, specials=True)):
+        expect = c_oracle.sum_f32_bits(x)
+        for mis in (0, 1, 2, 3):
+            assert gpu32(x, mis) == expect, mis
+
+
+@pytest.mark.parametrize("N", [255, 256, 257, 4096, 1_000_001])
+def test_repeats(N):
+    for v in (0.1, -3.0e38, 1.4e-45):
+        b = np.full(N, np.array([v], dtype=np.float32).view(np.uint32)[0], dtype=np.uint32)
+        assert gpu32(b) == c_oracle.sum_f32_bits(b)
+
+
+def test_full_size_2e8():
+    x = rand32(0, 2 * 10 ** 8, -60, 60)
+    assert gpu32(x) == c_oracle.sum_f32_bits(x)
