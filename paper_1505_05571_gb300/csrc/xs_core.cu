@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   unsigned f = T.flags();
   if (blockIdx.x == 0 && tid == 0 && a.n > 0) f |= kFlagAny;
   block_small_to_global<BLOCK>(smem_small, a, f, T.nkey);
-  finish_grid(a);
+  finish_grid(a, smem_small);
 }
 
 // ---------------------------------------------------------------------------
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_sum_large(SumArgs a) {
     if (f) atomicOr(&a.g->flags, f);
     if (L.nan_key) atomicMax(&a.g->nan_key, L.nan_key);
   }
-  finish_grid(a);
+  finish_grid(a, reinterpret_cast<long long*>(L.chunk));
 }
 
 // ---------------------------------------------------------------------------
@@ -186,11 +186,12 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_sum_large(SumArgs a) {
 // dst += src (chunkwise integer add of normalised accumulators, Discussion),
 // flags OR-ed, NaN keys maximised, then renormalised. One warp.
 __global__ void k_acc_merge(AccState* dst, const AccState* src) {
+  __shared__ long long sc[kSChunks];
   const int lane = threadIdx.x;
   long long v0 = dst->chunk[lane] + src->chunk[lane];
   long long v1 = dst->chunk[lane + 32] + src->chunk[lane + 32];
   long long v2 = lane < 3 ? dst->chunk[lane + 64] + src->chunk[lane + 64] : 0;
-  warp_normalize(v0, v1, v2);
+  warp_normalize(v0, v1, v2, sc, 1);
   dst->chunk[lane] = v0;
   dst->chunk[lane + 32] = v1;
   if (lane < 3) dst->chunk[lane + 64] = v2;
@@ -203,12 +204,13 @@ __global__ void k_acc_merge(AccState* dst, const AccState* src) {
 // Rounded value of an accumulator, or of its value divided by d >= 1; the
 // state is left unchanged. One warp.
 __global__ void k_acc_round(const AccState* s, double* out, unsigned long long d) {
+  __shared__ long long sc[kSChunks];
   const int lane = threadIdx.x;
   const long long v0 = s->chunk[lane];
   const long long v1 = s->chunk[lane + 32];
   const long long v2 = lane < 3 ? s->chunk[lane + 64] : 0;
-  const unsigned long long bits = d ? warp_round_div(v0, v1, v2, s->flags, s->nan_key, d)
-                                    : warp_round(v0, v1, v2, s->flags, s->nan_key);
+  const unsigned long long bits = d ? warp_round_div(v0, v1, v2, s->flags, s->nan_key, d, sc, 1)
+                                    : warp_round(v0, v1, v2, s->flags, s->nan_key, sc, 1);
   if (lane == 0) *reinterpret_cast<unsigned long long*>(out) = bits;
 }
 

@@ -329,16 +329,21 @@ __device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit)
 // Lane L holds chunks L (v0), L+32 (v1) and L+64 (v2, lanes 0..2 only).
 // --------------------------------------------------------------------------
 
-// Parallel carry propagation: every round moves each chunk's signed high part
-// one chunk up. After two rounds all carries are -1, 0 or +1 and travel one
-// chunk per round, so at most 69 rounds reach the canonical form.
-__device__ __forceinline__ void warp_normalize(long long& v0, long long& v1, long long& v2) {
+// Carry propagation of a warp-spread accumulator. Two parallel rounds move
+// every chunk's signed high part one chunk up; after them the remaining
+// carries are -1, 0 or +1 and can only ripple through chunks equal to 0 or
+// 2^32 - 1 (the typical case is a negative value, whose canonical chunks are
+// 2^32 - 1 all the way up). If any carry is left, one lane finishes the
+// propagation sequentially through `sc` (67 long longs, stride ss, owned by
+// this warp).
+__device__ __noinline__ static void warp_normalize(long long& v0, long long& v1, long long& v2,
+                                                   long long* sc, int ss) {
   const int lane = threadIdx.x & 31;
-  for (int it = 0; it < 80; ++it) {
+  for (int it = 0; it < 2; ++it) {
     const long long c0 = v0 >> 32;
     const long long c1 = v1 >> 32;
     const long long c2 = (lane < 2) ? (v2 >> 32) : 0;  // chunk 66 keeps its high part
-    if (!__any_sync(kFull, (c0 | c1 | c2) != 0)) break;
+    if (!__any_sync(kFull, (c0 | c1 | c2) != 0)) return;
     v0 &= 0xFFFFFFFFll;
     v1 &= 0xFFFFFFFFll;
     if (lane < 2) v2 &= 0xFFFFFFFFll;
@@ -356,6 +361,26 @@ __device__ __forceinline__ void warp_normalize(long long& v0, long long& v1, lon
     v1 += u1;
     v2 += u2;
   }
+  const bool left = ((v0 >> 32) | (v1 >> 32) | ((lane < 2) ? (v2 >> 32) : 0)) != 0;
+  if (!__any_sync(kFull, left)) return;
+  sc[lane * ss] = v0;
+  sc[(lane + 32) * ss] = v1;
+  if (lane < 3) sc[(lane + 64) * ss] = v2;
+  __syncwarp();
+  if (lane == 0) {
+    long long carry = 0;
+    for (int k = 0; k < kSChunks - 1; ++k) {
+      const long long x = sc[k * ss] + carry;
+      sc[k * ss] = x & 0xFFFFFFFFll;
+      carry = x >> 32;
+    }
+    sc[(kSChunks - 1) * ss] += carry;
+  }
+  __syncwarp();
+  v0 = sc[lane * ss];
+  v1 = sc[(lane + 32) * ss];
+  v2 = lane < 3 ? sc[(lane + 64) * ss] : 0;
+  __syncwarp();
 }
 
 __device__ __forceinline__ unsigned lanes_below(int x) {
@@ -363,16 +388,29 @@ __device__ __forceinline__ unsigned lanes_below(int x) {
 }
 
 // Normalise and take the magnitude; returns whether the value is negative.
-__device__ __forceinline__ bool warp_abs(long long& v0, long long& v1, long long& v2) {
-  warp_normalize(v0, v1, v2);
-  const bool neg = __shfl_sync(kFull, v2, 2) < 0;
-  if (neg) {
-    v0 = -v0;
-    v1 = -v1;
-    v2 = -v2;
-    warp_normalize(v0, v1, v2);
-  }
-  return neg;
+// The negation of a canonical value is canonical at once: with j its lowest
+// nonzero chunk below the top, chunks under j stay 0, chunk j becomes
+// 2^32 - c_j, higher chunks 2^32 - 1 - c_k, and the top -c_66 - 1 (or -c_66
+// when every lower chunk is 0).
+__device__ __forceinline__ bool warp_abs(long long& v0, long long& v1, long long& v2,
+                                         long long* sc, int ss) {
+  const int lane = threadIdx.x & 31;
+  warp_normalize(v0, v1, v2, sc, ss);
+  if (__shfl_sync(kFull, v2, 2) >= 0) return false;
+  const unsigned b0 = __ballot_sync(kFull, v0 != 0);
+  const unsigned b1 = __ballot_sync(kFull, v1 != 0);
+  const unsigned b2 = __ballot_sync(kFull, lane < 2 && v2 != 0);
+  const int j = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : (b2 ? 64 + __ffs(b2) - 1 : 66));
+  auto neg = [&](long long c, int k) -> long long {
+    if (k == kSChunks - 1) return j < kSChunks - 1 ? -c - 1 : -c;
+    if (k < j) return 0;
+    if (k == j) return 4294967296ll - c;
+    return 4294967295ll - c;
+  };
+  v0 = neg(v0, lane);
+  v1 = neg(v1, lane + 32);
+  if (lane < 3) v2 = neg(v2, lane + 64);
+  return true;
 }
 
 // Round to nearest, ties to even, the magnitude A * 2^-1075 + (something in
@@ -447,10 +485,11 @@ __device__ __forceinline__ unsigned long long signed_zero(unsigned flags) {
 // are spread over the warp as above.
 __device__ __noinline__ static unsigned long long warp_round(long long v0, long long v1,
                                                              long long v2, unsigned flags,
-                                                             unsigned long long nan_key) {
+                                                             unsigned long long nan_key,
+                                                             long long* sc, int ss) {
   unsigned long long sp;
   if (special_result(flags, nan_key, &sp)) return sp;
-  const bool neg = warp_abs(v0, v1, v2);
+  const bool neg = warp_abs(v0, v1, v2, sc, ss);
   if (warp_is_zero(v0, v1, v2)) return signed_zero(flags);
   return warp_round_mag(v0, v1, v2, false) | (neg ? kNegZero : 0ull);
 }
@@ -518,10 +557,11 @@ __device__ __noinline__ static bool warp_divide(long long& v0, long long& v1, lo
 __device__ __noinline__ static unsigned long long warp_round_div(long long v0, long long v1,
                                                                  long long v2, unsigned flags,
                                                                  unsigned long long nan_key,
-                                                                 unsigned long long d) {
+                                                                 unsigned long long d,
+                                                                 long long* sc, int ss) {
   unsigned long long sp;
   if (special_result(flags, nan_key, &sp)) return sp;
-  const bool neg = warp_abs(v0, v1, v2);
+  const bool neg = warp_abs(v0, v1, v2, sc, ss);
   if (warp_is_zero(v0, v1, v2)) return signed_zero(flags);
   const bool sticky = warp_divide(v0, v1, v2, d);
   return warp_round_mag(v0, v1, v2, sticky) | (neg ? kNegZero : 0ull);

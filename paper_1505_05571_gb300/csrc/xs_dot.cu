@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_dot_small(DotArgs d) {
   unsigned f = T.flags();
   if (blockIdx.x == 0 && tid == 0 && a.n > 0) f |= kFlagAny;
   block_small_to_global<BLOCK>(smem_dot, a, f, T.nkey);
-  finish_grid(a);
+  finish_grid(a, smem_dot);
 }
 
 namespace {

@@ -2,7 +2,7 @@
 //
 // Each segment is summed exactly and rounded once (abstract; small section on
 // rounding). Work decomposition, computed on the device from the offsets by
-// k_seg_prep:
+// k_seg_count / k_seg_scan / k_seg_fill:
 //   * long segments (length > short_max) are cut into tiles of tile_elems
 //     elements; a block sums a tile with per-thread small superaccumulators
 //     (Fig. 3). A one-tile segment is rounded by that block; the tiles of a
@@ -37,11 +37,19 @@ struct SegArgs {
   long long* short_list;       // nseg: indices of short segments
   AccState* slots;             // per multi-tile segment
   unsigned long long* counters;  // [0] tiles, [1] short segments, [2] tile cursor, [3] short cursor
+  long long* blk;               // 3 x nblk: per-block (tiles, short, slots), then their offsets
+  long long nblk;               // prep blocks of kPrepSegs segments
+  int* tile_seg;                // segment of each tile, when the tiles fit in tile_cap
+  long long tile_cap;
   long long tile_elems;
   long long short_max;
 };
 
-// Block-wide exclusive scan of one long long per thread (1024 threads).
+constexpr int kPrepThreads = 256;
+constexpr int kPrepPer = 8;                              // segments per prep thread
+constexpr int kPrepSegs = kPrepThreads * kPrepPer;       // segments per prep block
+
+// Block-wide exclusive scan of one long long per thread; `total` gets the sum.
 __device__ long long block_exclusive_scan(long long v, long long* total, long long* sbuf) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long incl = v;
@@ -71,48 +79,92 @@ __device__ long long block_exclusive_scan(long long v, long long* total, long lo
   return r;
 }
 
-// Work lists from the offsets. One block of 1024 threads; thread t owns a
-// contiguous run of segments.
-__global__ void __launch_bounds__(1024) k_seg_prep(SegArgs a) {
-  __shared__ long long sbuf[33];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const long long per = (a.nseg + nt - 1) / nt;
-  const long long s0 = min((long long)tid * per, a.nseg);
-  const long long s1 = min(s0 + per, a.nseg);
-  long long tiles = 0, nshort = 0, nslot = 0;
+// Work lists from the offsets, in three coalesced steps. A prep block owns
+// kPrepSegs consecutive segments, a thread kPrepPer of them; the order of the
+// lists is the order of the segments.
+struct SegCounts {
+  long long tiles, shorts, slots;
+};
+__device__ __forceinline__ SegCounts thread_counts(const SegArgs& a, long long s0, long long s1) {
+  SegCounts c{0, 0, 0};
   for (long long s = s0; s < s1; ++s) {
     const long long L = a.off[s + 1] - a.off[s];
     if (L > a.short_max) {
       const long long t = (L + a.tile_elems - 1) / a.tile_elems;
-      tiles += t;
-      nslot += (t > 1);
+      c.tiles += t;
+      c.slots += (t > 1);
     } else {
-      ++nshort;
+      ++c.shorts;
     }
   }
-  long long tot_tiles, tot_short, tot_slot;
-  long long t_off = block_exclusive_scan(tiles, &tot_tiles, sbuf);
-  long long sh_off = block_exclusive_scan(nshort, &tot_short, sbuf);
-  long long sl_off = block_exclusive_scan(nslot, &tot_slot, sbuf);
+  return c;
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_seg_count(SegArgs a) {
+  __shared__ long long sbuf[33];
+  const long long s0 = min((long long)blockIdx.x * kPrepSegs + (long long)threadIdx.x * kPrepPer, a.nseg);
+  const long long s1 = min(s0 + kPrepPer, a.nseg);
+  const SegCounts c = thread_counts(a, s0, s1);
+  long long tot[3];
+  block_exclusive_scan(c.tiles, &tot[0], sbuf);
+  block_exclusive_scan(c.shorts, &tot[1], sbuf);
+  block_exclusive_scan(c.slots, &tot[2], sbuf);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) a.blk[k * a.nblk + blockIdx.x] = tot[k];
+}
+
+// One block: exclusive scan of the block totals (in place) and the counters.
+__global__ void __launch_bounds__(1024) k_seg_scan(SegArgs a) {
+  __shared__ long long sbuf[33];
+  for (int k = 0; k < 3; ++k) {
+    long long carry = 0;
+    for (long long base = 0; base < a.nblk; base += blockDim.x) {
+      const long long i = base + threadIdx.x;
+      const long long v = i < a.nblk ? a.blk[k * a.nblk + i] : 0;
+      long long tot;
+      const long long ex = block_exclusive_scan(v, &tot, sbuf);
+      if (i < a.nblk) a.blk[k * a.nblk + i] = carry + ex;
+      carry += tot;
+    }
+    if (threadIdx.x == 0) {
+      if (k == 0) {
+        a.counters[0] = (unsigned long long)carry;
+        a.tile_start[a.nseg] = carry;
+      } else if (k == 1) {
+        a.counters[1] = (unsigned long long)carry;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.counters[2] = 0ull;
+    a.counters[3] = 0ull;
+  }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_seg_fill(SegArgs a) {
+  __shared__ long long sbuf[33];
+  const long long s0 = min((long long)blockIdx.x * kPrepSegs + (long long)threadIdx.x * kPrepPer, a.nseg);
+  const long long s1 = min(s0 + kPrepPer, a.nseg);
+  const SegCounts c = thread_counts(a, s0, s1);
+  long long tot;
+  long long t_off = a.blk[blockIdx.x] + block_exclusive_scan(c.tiles, &tot, sbuf);
+  long long sh_off = a.blk[a.nblk + blockIdx.x] + block_exclusive_scan(c.shorts, &tot, sbuf);
+  long long sl_off = a.blk[2 * a.nblk + blockIdx.x] + block_exclusive_scan(c.slots, &tot, sbuf);
   for (long long s = s0; s < s1; ++s) {
     const long long L = a.off[s + 1] - a.off[s];
     a.tile_start[s] = t_off;
     int slot = -1;
     if (L > a.short_max) {
       const long long t = (L + a.tile_elems - 1) / a.tile_elems;
+      if (t_off + t <= a.tile_cap)
+        for (long long k = 0; k < t; ++k) a.tile_seg[t_off + k] = (int)s;
       t_off += t;
       if (t > 1) slot = (int)(sl_off++);
     } else {
       a.short_list[sh_off++] = s;
     }
     a.slot_of[s] = slot;
-  }
-  if (tid == 0) {
-    a.tile_start[a.nseg] = tot_tiles;
-    a.counters[0] = (unsigned long long)tot_tiles;
-    a.counters[1] = (unsigned long long)tot_short;
-    a.counters[2] = 0ull;
-    a.counters[3] = 0ull;
   }
 }
 
@@ -141,13 +193,18 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     __syncthreads();
     const long long t = s_item;
     if (t >= ntiles) break;
-    // segment of tile t: last s with tile_start[s] <= t
-    long long lo_s = 0, hi_s = a.nseg;  // invariant: tile_start[lo_s] <= t < tile_start[hi_s]
-    while (hi_s - lo_s > 1) {
-      const long long mid = (lo_s + hi_s) >> 1;
-      if (a.tile_start[mid] <= t) lo_s = mid; else hi_s = mid;
+    // segment of tile t: from the table, else the last s with tile_start[s] <= t
+    long long s;
+    if (ntiles <= a.tile_cap) {
+      s = a.tile_seg[t];
+    } else {
+      long long lo_s = 0, hi_s = a.nseg;  // invariant: tile_start[lo_s] <= t < tile_start[hi_s]
+      while (hi_s - lo_s > 1) {
+        const long long mid = (lo_s + hi_s) >> 1;
+        if (a.tile_start[mid] <= t) lo_s = mid; else hi_s = mid;
+      }
+      s = lo_s;
     }
-    const long long s = lo_s;
     const long long first_tile = a.tile_start[s];
     const long long seg_tiles = a.tile_start[s + 1] - first_tile;
     const long long seg_lo = a.off[s], seg_hi = a.off[s + 1];
@@ -173,7 +230,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
         (void)bits;
         const unsigned long long r = warp_round(bsum[lane], bsum[lane + 32],
                                                 lane < 3 ? bsum[lane + 64] : 0,
-                                                s_flags | kFlagAny, s_nkey);
+                                                s_flags | kFlagAny, s_nkey, smem_seg, 1);
         if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
       }
     } else {
@@ -204,7 +261,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
         }
         fl = __shfl_sync(kFull, fl, 0);
         key = __shfl_sync(kFull, key, 0);
-        const unsigned long long r = warp_round(v0, v1, v2, fl | kFlagAny, key);
+        const unsigned long long r = warp_round(v0, v1, v2, fl | kFlagAny, key, smem_seg, 1);
         if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
       }
     }
@@ -213,13 +270,23 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
 
   // ---- phase 2: short segments, one warp each ----
   const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
+  constexpr long long kClaim = 32;  // short segments a warp claims per cursor atomic
   for (;;) {
-    long long j = 0;
-    if (lane == 0) j = (long long)atomicAdd(&a.counters[3], 1ull);
-    j = __shfl_sync(kFull, j, 0);
-    if (j >= nshort) break;
-    const long long s = a.short_list[j];
-    const long long lo = a.off[s], hi = a.off[s + 1];
+    long long j0 = 0;
+    if (lane == 0) j0 = (long long)atomicAdd(&a.counters[3], (unsigned long long)kClaim);
+    j0 = __shfl_sync(kFull, j0, 0);
+    if (j0 >= nshort) break;
+    const int cnt = (int)min(kClaim, nshort - j0);
+    // lane q fetches the metadata of the q-th claimed segment, all at once
+    long long ms = 0, mlo = 0, mhi = 0;
+    if (lane < cnt) {
+      ms = a.short_list[j0 + lane];
+      mlo = a.off[ms];
+      mhi = a.off[ms + 1];
+    }
+    for (int q = 0; q < cnt; ++q) {
+    const long long s = __shfl_sync(kFull, ms, q);
+    const long long lo = __shfl_sync(kFull, mlo, q), hi = __shfl_sync(kFull, mhi, q);
     const long long L = hi - lo;
     if (L <= 2) {
       const unsigned long long b0 = L > 0 ? xb[lo] : 0ull;
@@ -235,22 +302,55 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
         continue;
       }
     }
-    for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
     T.reset();
-    accumulate_range<BLOCK, 2, false>(T, a.x, lo, hi, lane, 32);
+    int cmin = 0, cmax = kSChunks - 1;  // chunks the warp's terms can touch
+    if (L <= 128) {
+      // Low fixed cost for short sums (Discussion: track the chunks in use
+      // instead of clearing and scanning all 67): the terms sit in registers,
+      // the warp finds the range of chunk indices they touch, and only that
+      // window is cleared, added into and read back.
+      unsigned long long v[4];
+      int mn = kSChunks, mx = -1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const long long idx = lo + lane + 32 * k;
+        v[k] = idx < hi ? xb[idx] : kNegZero;
+        const unsigned e = (unsigned)(v[k] >> 52) & 0x7FFu;
+        if (e != 0x7FFu && (v[k] << 1) != 0ull) {  // finite and nonzero
+          const int i = (int)((e ? e : 1u) >> kLowExpBits);
+          mn = min(mn, i);
+          mx = max(mx, i + 1);
+        }
+      }
+      cmin = __reduce_min_sync(kFull, mn);
+      cmax = __reduce_max_sync(kFull, mx);
+      for (int c = cmin; c <= cmax; ++c) T.acc[c * BLOCK] = 0;
+      // zeros outside the window add 0 to chunks that are never read
+#pragma unroll
+      for (int k = 0; k < 4; ++k) T.one<BLOCK>(v[k]);
+    } else {
+      for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
+      accumulate_range<BLOCK, 2, false>(T, a.x, lo, hi, lane, 32);
+    }
     __syncwarp();
-    // lane L gathers chunks L, L+32, L+64 of the warp's 32 accumulators, split
-    // into low and high halves; reads are rotated by lane to avoid conflicts
+    // lane L gathers chunks L, L+32, L+64 of the warp's 32 accumulators (only
+    // those in the window), split into low and high halves; reads are rotated
+    // by lane to avoid conflicts
     const long long* wbase = smem_seg + warp * 32;
     long long lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0, lo2 = 0, hi2 = 0;
-    for (int q = 0; q < 32; ++q) {
-      const int src = (q + lane) & 31;
-      const long long u0 = wbase[lane * BLOCK + src];
-      const long long u1 = wbase[(lane + 32) * BLOCK + src];
-      const long long u2 = lane < 3 ? wbase[(lane + 64) * BLOCK + src] : 0;
-      lo0 += u0 & 0xFFFFFFFFll; hi0 += u0 >> 32;
-      lo1 += u1 & 0xFFFFFFFFll; hi1 += u1 >> 32;
-      lo2 += u2 & 0xFFFFFFFFll; hi2 += u2 >> 32;
+    const bool in0w = lane >= cmin && lane <= cmax;
+    const bool in1w = lane + 32 >= cmin && lane + 32 <= cmax;
+    const bool in2w = lane < 3 && lane + 64 >= cmin && lane + 64 <= cmax;
+    if (in0w | in1w | in2w) {
+      for (int q = 0; q < 32; ++q) {
+        const int src = (q + lane) & 31;
+        const long long u0 = in0w ? wbase[lane * BLOCK + src] : 0;
+        const long long u1 = in1w ? wbase[(lane + 32) * BLOCK + src] : 0;
+        const long long u2 = in2w ? wbase[(lane + 64) * BLOCK + src] : 0;
+        lo0 += u0 & 0xFFFFFFFFll; hi0 += u0 >> 32;
+        lo1 += u1 & 0xFFFFFFFFll; hi1 += u1 >> 32;
+        lo2 += u2 & 0xFFFFFFFFll; hi2 += u2 >> 32;
+      }
     }
     // high half of chunk c belongs to chunk c+1 (chunk 66 keeps its own)
     const long long top_hi = (lane == 2) ? hi2 : 0;
@@ -265,9 +365,11 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     const long long v2 = lane < 3 ? lo2 + in2 + top_hi * 4294967296ll : 0;
     const unsigned f = __reduce_or_sync(kFull, T.flags()) | kFlagAny;
     const unsigned long long key = warp_max_ull(T.nkey);
-    const unsigned long long r = warp_round(v0, v1, v2, f, key);
+    __syncwarp();  // every lane's gather is done: column 0 of the warp is scratch now
+    const unsigned long long r = warp_round(v0, v1, v2, f, key, smem_seg + warp * 32, BLOCK);
     if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
     __syncwarp();
+    }
   }
 }
 
@@ -339,7 +441,12 @@ struct xs_seg_plan_s {
 };
 
 static xs_status plan_enqueue(xs_seg_plan p, cudaStream_t s) {
-  k_seg_prep<<<1, 1024, 0, s>>>(p->args);
+  const unsigned nb = (unsigned)p->args.nblk;
+  k_seg_count<<<nb, kPrepThreads, 0, s>>>(p->args);
+  XS_TRY_CUDA(cudaGetLastError());
+  k_seg_scan<<<1, 1024, 0, s>>>(p->args);
+  XS_TRY_CUDA(cudaGetLastError());
+  k_seg_fill<<<nb, kPrepThreads, 0, s>>>(p->args);
   XS_TRY_CUDA(cudaGetLastError());
   const SegEntry& K = kSeg[p->kernel];
   K.fn<<<p->grid, K.block, seg_smem(K.block), s>>>(p->args);
@@ -390,7 +497,22 @@ xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const in
   // multi-tile segments: at most total/tile, and at most nseg
   const size_t max_slots = n;
   const size_t bytes_slots = max_slots * sizeof(AccState);
-  const size_t total = bytes_ctr + bytes_ts + bytes_sl + bytes_so + bytes_slots;
+  const size_t nblk = (n + kPrepSegs - 1) / kPrepSegs;
+  const size_t bytes_blk = 3 * nblk * sizeof(long long);
+  // tile table sized for the offsets as they are now (segments + elements / tile)
+  long long last = 0;
+  cudaError_t e0 = cudaMemcpy(&last, d_offsets + nseg, sizeof(long long), cudaMemcpyDeviceToHost);
+  if (e0 != cudaSuccess) {
+    delete p;
+    return from_cuda(e0);
+  }
+  if (last < 0) {
+    delete p;
+    return set_error(XS_ERR_INVALID_VALUE);
+  }
+  const size_t tile_cap = n + (size_t)(last / o.tile_elems) + 1;
+  const size_t bytes_tab = ((tile_cap * sizeof(int) + 15) / 16) * 16;
+  const size_t total = bytes_ctr + bytes_ts + bytes_sl + bytes_so + bytes_slots + bytes_blk + bytes_tab;
   cudaError_t e = cudaMalloc(&p->mem, total);
   if (e != cudaSuccess) {
     delete p;
@@ -414,6 +536,11 @@ xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const in
   a.short_list = reinterpret_cast<long long*>(base + bytes_ctr + bytes_ts);
   a.slot_of = reinterpret_cast<int*>(base + bytes_ctr + bytes_ts + bytes_sl);
   a.slots = reinterpret_cast<AccState*>(base + bytes_ctr + bytes_ts + bytes_sl + bytes_so);
+  a.blk = reinterpret_cast<long long*>(base + bytes_ctr + bytes_ts + bytes_sl + bytes_so + bytes_slots);
+  a.nblk = (long long)nblk;
+  a.tile_seg = reinterpret_cast<int*>(base + bytes_ctr + bytes_ts + bytes_sl + bytes_so + bytes_slots +
+                                      bytes_blk);
+  a.tile_cap = (long long)tile_cap;
   a.tile_elems = o.tile_elems;
   a.short_max = o.short_max;
   // capture prep + main into a graph on a private stream
@@ -451,7 +578,7 @@ xs_status xs_seg_plan_launch_direct(xs_seg_plan p, void* stream) {
   return set_error(XS_OK);
 }
 
-int xs_seg_plan_kernel_launches(xs_seg_plan p) { return p ? 2 : 0; }
+int xs_seg_plan_kernel_launches(xs_seg_plan p) { return p ? 4 : 0; }
 
 xs_status xs_seg_plan_destroy(xs_seg_plan p) {
   if (p == nullptr) return set_error(XS_ERR_INVALID_POINTER);
