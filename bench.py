@@ -52,6 +52,8 @@ KERNEL_SOURCES = {
     "k_sum_large": [("xs_kernels.cuh", None, None),
                     ("xs_core.cu", "// Large superaccumulator kernel", "// Accumulator-handle kernels")],
     "k_seg_main": [("xs_segments.cu", "struct SegArgs {", "namespace {")],
+    "k_dot_small": [("xs_kernels.cuh", None, None), ("xs_dot.cu", None, None)],
+    "k_sum_f32": [("xs_f32.cu", None, None)],
 }
 
 
@@ -314,7 +316,58 @@ def extra_configs(torch, np, xsum, devgen, W, dev, stream, rate_gbs, xd, n):
         out["cfg3_segmented"] = {"skipped": f"needs {total * 8 / 2**30:.1f} GiB free"}
 
     out["cfg4_serving"] = serving_report(torch, np, xsum, devgen, dev, stream, rate_gbs)
+    out["next_rows"] = next_rows(torch, np, xsum, devgen, dev, stream, xd, n)
     return out
+
+
+def next_rows(torch, np, xsum, devgen, dev, stream, xd, n):
+    """Exact mean, dot product, squared norm, binary32 sum and tiny segments, each
+    beside the inexact device routine that computes the same quantity."""
+    r = {}
+    res = torch.empty(1, dtype=torch.float64, device=dev)
+    gbs = lambda b, ms: round(b / (ms * 1e-3) / 1e9, 1)  # noqa: E731
+    t = med_time(torch, stream, lambda: xsum.xs_mean_async(xd, n, res, stream), reps=10)
+    r["mean_cfg1"] = {"us": round(t * 1000, 1), "gbs": gbs(8 * n, t)}
+    y = torch.empty(n, dtype=torch.int64, device=dev)
+    devgen.band(y, 1, 0)
+    yd = y.view(torch.float64)
+    t = med_time(torch, stream, lambda: xsum.xs_dot_async(xd, yd, n, res, stream), reps=10)
+    ti = med_time(torch, stream, lambda: torch.dot(xd, yd), reps=10)
+    r["dot_cfg1"] = {"us": round(t * 1000, 1), "gbs": gbs(16 * n, t),
+                     "inexact_torch_dot_us": round(ti * 1000, 1)}
+    t = med_time(torch, stream, lambda: xsum.xs_norm2_async(xd, n, res, stream), reps=10)
+    ti = med_time(torch, stream, lambda: torch.dot(xd, xd), reps=10)
+    r["norm2_cfg1"] = {"us": round(t * 1000, 1), "gbs": gbs(8 * n, t),
+                       "inexact_torch_dot_us": round(ti * 1000, 1),
+                       "bound": "fp64 multiply pipe (0.53 T/s measured: 189 us for 1e8 products)"}
+    del y, yd
+    m = 2 * 10 ** 8
+    rng = np.random.default_rng(0)
+    h = ((rng.integers(67, 187, m, dtype=np.uint32) << np.uint32(23))
+         | rng.integers(0, 1 << 23, m, dtype=np.uint32)
+         | (rng.integers(0, 2, m, dtype=np.uint32) << np.uint32(31)))
+    f = torch.from_numpy(h.view(np.int32)).to(dev).view(torch.float32)
+    o32 = torch.empty(1, dtype=torch.float32, device=dev)
+    t = med_time(torch, stream, lambda: xsum.xs_sum_f32_async(f, m, o32, stream), reps=10)
+    ti = med_time(torch, stream, lambda: torch.sum(f), reps=10)
+    r["f32_2e8"] = {"us": round(t * 1000, 1), "gbs": gbs(4 * m, t),
+                    "inexact_torch_sum_us": round(ti * 1000, 1)}
+    del f
+    from workloads import gen
+    lengths = np.random.default_rng(0).integers(1, 101, 2_000_000).astype(np.int64)
+    off = gen.cfg3_offsets(lengths)
+    v = torch.empty(int(off[-1]), dtype=torch.int64, device=dev)
+    devgen.band(v, 1, 0, -30, 30)
+    od = torch.from_numpy(off).to(dev)
+    so = torch.empty(lengths.size, dtype=torch.float64, device=dev)
+    plan = xsum.xs_seg_plan_create(v.view(torch.float64), od, lengths.size, so, None, stream)
+    t = med_time(torch, stream, lambda: xsum.xs_seg_plan_launch(plan, stream), reps=10)
+    xsum.xs_seg_plan_destroy(plan)
+    r["tiny_segments_2e6_len1to100"] = {"ms": round(t, 3),
+                                        "segments_per_s": round(lengths.size / (t * 1e-3), 0)}
+    del v
+    torch.cuda.empty_cache()
+    return r
 
 
 def serving_report(torch, np, xsum, devgen, dev, stream, rate_gbs, n_arrivals=4000, seed=7):

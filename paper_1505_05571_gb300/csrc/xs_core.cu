@@ -191,7 +191,7 @@ __global__ void k_acc_merge(AccState* dst, const AccState* src) {
   long long v0 = dst->chunk[lane] + src->chunk[lane];
   long long v1 = dst->chunk[lane + 32] + src->chunk[lane + 32];
   long long v2 = lane < 3 ? dst->chunk[lane + 64] + src->chunk[lane + 64] : 0;
-  warp_normalize(v0, v1, v2, sc, 1);
+  warp_normalize(v0, v1, v2, sc, 32);
   dst->chunk[lane] = v0;
   dst->chunk[lane + 32] = v1;
   if (lane < 3) dst->chunk[lane + 64] = v2;
@@ -209,8 +209,8 @@ __global__ void k_acc_round(const AccState* s, double* out, unsigned long long d
   const long long v0 = s->chunk[lane];
   const long long v1 = s->chunk[lane + 32];
   const long long v2 = lane < 3 ? s->chunk[lane + 64] : 0;
-  const unsigned long long bits = d ? warp_round_div(v0, v1, v2, s->flags, s->nan_key, d, sc, 1)
-                                    : warp_round(v0, v1, v2, s->flags, s->nan_key, sc, 1);
+  const unsigned long long bits = d ? warp_round_div(v0, v1, v2, s->flags, s->nan_key, d, sc, 32)
+                                    : warp_round(v0, v1, v2, s->flags, s->nan_key, sc, 32);
   if (lane == 0) *reinterpret_cast<unsigned long long*>(out) = bits;
 }
 

@@ -334,8 +334,9 @@ __device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit)
 // carries are -1, 0 or +1 and can only ripple through chunks equal to 0 or
 // 2^32 - 1 (the typical case is a negative value, whose canonical chunks are
 // 2^32 - 1 all the way up). If any carry is left, one lane finishes the
-// propagation sequentially through `sc` (67 long longs, stride ss, owned by
-// this warp).
+// propagation sequentially through the warp's scratch: chunk k lives at
+// sc[(k >> 5) * ss + (k & 31)] (ss = 32: 67 consecutive long longs), so the
+// lanes' stores and loads never conflict.
 __device__ __noinline__ static void warp_normalize(long long& v0, long long& v1, long long& v2,
                                                    long long* sc, int ss) {
   const int lane = threadIdx.x & 31;
@@ -363,23 +364,24 @@ __device__ __noinline__ static void warp_normalize(long long& v0, long long& v1,
   }
   const bool left = ((v0 >> 32) | (v1 >> 32) | ((lane < 2) ? (v2 >> 32) : 0)) != 0;
   if (!__any_sync(kFull, left)) return;
-  sc[lane * ss] = v0;
-  sc[(lane + 32) * ss] = v1;
-  if (lane < 3) sc[(lane + 64) * ss] = v2;
+  sc[lane] = v0;
+  sc[ss + lane] = v1;
+  if (lane < 3) sc[2 * ss + lane] = v2;
   __syncwarp();
   if (lane == 0) {
     long long carry = 0;
     for (int k = 0; k < kSChunks - 1; ++k) {
-      const long long x = sc[k * ss] + carry;
-      sc[k * ss] = x & 0xFFFFFFFFll;
+      long long* p = sc + (k >> 5) * ss + (k & 31);
+      const long long x = *p + carry;
+      *p = x & 0xFFFFFFFFll;
       carry = x >> 32;
     }
-    sc[(kSChunks - 1) * ss] += carry;
+    sc[2 * ss + 2] += carry;
   }
   __syncwarp();
-  v0 = sc[lane * ss];
-  v1 = sc[(lane + 32) * ss];
-  v2 = lane < 3 ? sc[(lane + 64) * ss] : 0;
+  v0 = sc[lane];
+  v1 = sc[ss + lane];
+  v2 = lane < 3 ? sc[2 * ss + lane] : 0;
   __syncwarp();
 }
 

@@ -44,14 +44,14 @@ static __device__ void finish_grid(const SumArgs& a, long long* sc) {
     }
     flags = __shfl_sync(kFull, flags, 0);
     key = __shfl_sync(kFull, key, 0);
-    const unsigned long long bits = a.divisor ? warp_round_div(v0, v1, v2, flags, key, a.divisor, sc, 1)
-                                              : warp_round(v0, v1, v2, flags, key, sc, 1);
+    const unsigned long long bits = a.divisor ? warp_round_div(v0, v1, v2, flags, key, a.divisor, sc, 32)
+                                              : warp_round(v0, v1, v2, flags, key, sc, 32);
     if (lane == 0) *reinterpret_cast<unsigned long long*>(a.out) = bits;
   } else {
     long long v0 = (long long)__ldcg(ch + lane);
     long long v1 = (long long)__ldcg(ch + lane + 32);
     long long v2 = lane < 3 ? (long long)__ldcg(ch + lane + 64) : 0;
-    warp_normalize(v0, v1, v2, sc, 1);
+    warp_normalize(v0, v1, v2, sc, 32);
     ch[lane] = (unsigned long long)v0;
     ch[lane + 32] = (unsigned long long)v1;
     if (lane < 3) ch[lane + 64] = (unsigned long long)v2;

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
         (void)bits;
         const unsigned long long r = warp_round(bsum[lane], bsum[lane + 32],
                                                 lane < 3 ? bsum[lane + 64] : 0,
-                                                s_flags | kFlagAny, s_nkey, smem_seg, 1);
+                                                s_flags | kFlagAny, s_nkey, smem_seg, 32);
         if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
       }
     } else {
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
         }
         fl = __shfl_sync(kFull, fl, 0);
         key = __shfl_sync(kFull, key, 0);
-        const unsigned long long r = warp_round(v0, v1, v2, fl | kFlagAny, key, smem_seg, 1);
+        const unsigned long long r = warp_round(v0, v1, v2, fl | kFlagAny, key, smem_seg, 32);
         if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
       }
     }

@@ -130,13 +130,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
         }
         fl = __shfl_sync(kFull, fl, 0);
         key = __shfl_sync(kFull, key, 0);
-        const unsigned long long r = warp_round(v0, v1, v2, fl, key, smem_srv, 1);
+        const unsigned long long r = warp_round(v0, v1, v2, fl, key, smem_srv, 32);
         if (lane == 0 && it.res_idx >= 0) a.results[it.res_idx] = r;
       } else {  // keep the exact sum, in canonical form
         long long v0 = (long long)__ldcg(gc + lane);
         long long v1 = (long long)__ldcg(gc + lane + 32);
         long long v2 = lane < 3 ? (long long)__ldcg(gc + lane + 64) : 0;
-        warp_normalize(v0, v1, v2, smem_srv, 1);
+        warp_normalize(v0, v1, v2, smem_srv, 32);
         gc[lane] = (unsigned long long)v0;
         gc[lane + 32] = (unsigned long long)v1;
         if (lane < 3) gc[lane + 64] = (unsigned long long)v2;

@@ -1,0 +1,98 @@
+"""Runs one library entry point on one synthetic workload (for timing and ncu).
+
+    python -m workloads.cases <case> [--reps N]
+
+Cases: sum_cfg1, mean_cfg1, large_cfg1, dot_cfg1, norm2_cfg1, f32_2e8,
+seg_cfg3_5k (5,000 segments of the config-3 length law), seg_tiny (2,000,000
+segments of 1..100 values). Inputs are generated on the device; the case prints
+its median CUDA-event time. This module only calls the library.
+"""
+
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def build_case(name: str):
+    import numpy as np
+    import torch
+
+    from paper_1505_05571_gb300 import xsum
+    from workloads import devgen, gen
+
+    dev = torch.device("cuda", 0)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    if name in ("sum_cfg1", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1"):
+        n = 10 ** 8
+        x = torch.empty(n, dtype=torch.int64, device=dev)
+        devgen.band(x, 0, 0)
+        xd = x.view(torch.float64)
+        if name == "sum_cfg1":
+            return (lambda: xsum.xs_sum_async(xd, n, out)), 8 * n, (x,)
+        if name == "mean_cfg1":
+            return (lambda: xsum.xs_mean_async(xd, n, out)), 8 * n, (x,)
+        if name == "large_cfg1":
+            return (lambda: xsum.xs_sum_async(xd, n, out, xsum.XS_METHOD_LARGE)), 8 * n, (x,)
+        if name == "norm2_cfg1":
+            return (lambda: xsum.xs_norm2_async(xd, n, out)), 8 * n, (x,)
+        y = torch.empty(n, dtype=torch.int64, device=dev)
+        devgen.band(y, 1, 0)
+        yd = y.view(torch.float64)
+        return (lambda: xsum.xs_dot_async(xd, yd, n, out)), 16 * n, (x, y)
+    if name == "f32_2e8":
+        m = 2 * 10 ** 8
+        rng = np.random.default_rng(0)
+        h = ((rng.integers(67, 187, m, dtype=np.uint32) << np.uint32(23))
+             | rng.integers(0, 1 << 23, m, dtype=np.uint32)
+             | (rng.integers(0, 2, m, dtype=np.uint32) << np.uint32(31)))
+        f = torch.from_numpy(h.view(np.int32)).to(dev)
+        o32 = torch.empty(1, dtype=torch.float32, device=dev)
+        fd = f.view(torch.float32)
+        return (lambda: xsum.xs_sum_f32_async(fd, m, o32)), 4 * m, (f,)
+    if name in ("seg_cfg3_5k", "seg_tiny"):
+        if name == "seg_cfg3_5k":
+            lengths = gen.cfg3_lengths(0, 5000, 10 ** 6)
+        else:
+            lengths = np.random.default_rng(0).integers(1, 101, 2_000_000).astype(np.int64)
+        off = gen.cfg3_offsets(lengths)
+        total = int(off[-1])
+        v = torch.empty(total, dtype=torch.int64, device=dev)
+        devgen.band(v, 0, 0, -30, 30)
+        od = torch.from_numpy(off).to(dev)
+        so = torch.empty(lengths.size, dtype=torch.float64, device=dev)
+        plan = xsum.xs_seg_plan_create(v.view(torch.float64), od, lengths.size, so)
+        return (lambda: xsum.xs_seg_plan_launch(plan)), 8 * total, (v, od, so)
+    raise SystemExit(f"unknown case {name}")
+
+
+def main():
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case")
+    ap.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args()
+    fn, nbytes, _keep = build_case(args.case)
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    t = times[len(times) // 2]
+    print(f"{args.case}: {t * 1000:.1f} us, {nbytes / (t * 1e-3) / 1e9:.1f} GB/s")
+
+
+if __name__ == "__main__":
+    main()
