@@ -45,15 +45,16 @@ def read_peaks():
 
 # Source regions that define each profiled kernel: the shared device header
 # plus the kernel's own section of its translation unit.
+PREFETCH_DEFAULTS = ("xs_host.hpp", "int prefetch_tiles(int builtin);", "inline cudaStream_t as_stream")
 KERNEL_SOURCES = {
     "k_sum_small": [("xs_kernels.cuh", None, None),
                     ("xs_core.cu", "__device__ __forceinline__ void load_tile(",
-                     "// Large superaccumulator kernel")],
+                     "// Large superaccumulator kernel"), PREFETCH_DEFAULTS],
     "k_sum_large": [("xs_kernels.cuh", None, None),
                     ("xs_core.cu", "// Large superaccumulator kernel", "// Accumulator-handle kernels")],
     "k_seg_main": [("xs_segments.cu", "struct SegArgs {", "namespace {")],
-    "k_dot_small": [("xs_kernels.cuh", None, None), ("xs_dot.cu", None, None)],
-    "k_sum_f32": [("xs_f32.cu", None, None)],
+    "k_dot_small": [("xs_kernels.cuh", None, None), ("xs_dot.cu", None, None), PREFETCH_DEFAULTS],
+    "k_sum_f32": [("xs_f32.cu", None, None), PREFETCH_DEFAULTS],
 }
 
 
@@ -531,6 +532,17 @@ def run_ours(args):
         r = xsum.xs_sum_host(hd, n, stream)
     t_e2e = max_over_ranks(torch, (time.perf_counter() - t0) / e2e_steps, dev)
     same = (np.array([r0, r]).view(np.int64) == bits_last).all()
+    # the host link alone: one plain pinned H2D copy of the same 800 MB (no summation)
+    link = torch.empty(n, dtype=torch.int64, device=dev)
+    t_link = []
+    for _ in range(3):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        link.copy_(h, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        t_link.append(time.perf_counter() - t0)
+    link_gbs = 8.0 * n / min(t_link) / 1e9
+    del link
 
     if rank != 0:
         dist.destroy_process_group()
@@ -586,6 +598,8 @@ def run_ours(args):
             "d2h_bytes_per_step": 8,
             "api": "xs_sum_host (pinned host buffer, chunked H2D pipelined with accumulation)",
             "same_bits_as_device_path": bool(same),
+            "host_link_copy_gbs": round(link_gbs, 2),
+            "frac_of_host_link": round(8.0 * n / t_e2e / 1e9 / link_gbs, 4),
         },
         "gpu_launches": args.steps,
         "clocks": clk.summary(),

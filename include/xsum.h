@@ -109,8 +109,10 @@ xs_status xs_sum_async_config(const double* d_values, int64_t n, double* d_out, 
  * default. */
 xs_status xs_default_shape(int64_t n, int* method, int* block, int* unroll);
 
-/* L2 prefetch distance of the single-array kernels, in tiles of each block
- * (default 3; 0 disables). A process-wide tuning knob. */
+/* L2 prefetch distance of the sum, mean, dot, squared-norm and binary32
+ * kernels, in tiles of each block (0 disables, at most 64; -1, the initial
+ * setting, gives each kernel its built-in distance). A process-wide tuning
+ * knob. */
 xs_status xs_set_prefetch_tiles(int tiles);
 
 /* Number of compiled launch shapes, and shape k as (method, block, unroll). */

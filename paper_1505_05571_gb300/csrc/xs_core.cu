@@ -51,14 +51,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   const int tid = threadIdx.x;
   SmallThread T;
   T.acc = smem_small + tid;
-  for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
 
   const Split sp = split_input(a.x, a.n);
-  if (blockIdx.x == 0 && tid == 0) {
-    const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
-    if (sp.head) T.one<BLOCK>(xb[0]);
-    if (sp.tail) T.one<BLOCK>(xb[a.n - 1]);
-  }
   constexpr long long TP = (long long)BLOCK * UNROLL;
   const long long ntiles = (sp.npairs + TP - 1) / TP;
   const long long nfull = sp.npairs / TP;  // tiles without a ragged end
@@ -66,6 +60,15 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   long long t = blockIdx.x;
   if (tid == 0)
     for (int k = 1; k <= a.prefetch; ++k) prefetch_tile<BLOCK, UNROLL>(sp, t + k * G, ntiles);
+  // the first tile's loads are in flight while the accumulator is cleared
+  ulonglong2 A[UNROLL], B[UNROLL];
+  if (t < nfull) load_full<BLOCK, UNROLL>(sp, t, tid, A);
+  for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
+  if (blockIdx.x == 0 && tid == 0) {
+    const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
+    if (sp.head) T.one<BLOCK>(xb[0]);
+    if (sp.tail) T.one<BLOCK>(xb[a.n - 1]);
+  }
   int since = 0;
   auto tick = [&]() {
     if (++since >= a.carry_tiles) {
@@ -75,8 +78,6 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   };
   // Full tiles, two register buffers used in turn: the loads of the next
   // tile are in flight while the current one is added.
-  ulonglong2 A[UNROLL], B[UNROLL];
-  if (t < nfull) load_full<BLOCK, UNROLL>(sp, t, tid, A);
   while (t < nfull) {
     if (tid == 0 && a.prefetch > 0) prefetch_tile<BLOCK, UNROLL>(sp, t + (a.prefetch + 1) * G, ntiles);
     if (t + G < nfull) load_full<BLOCK, UNROLL>(sp, t + G, tid, B);
@@ -298,7 +299,7 @@ const KernelEntry kKernels[] = {
 };
 constexpr int kNumKernels = sizeof(kKernels) / sizeof(kKernels[0]);
 
-int g_prefetch_tiles = 3;  // L2 prefetch distance of the single-array kernels, in tiles
+int g_prefetch_tiles = -1;  // L2 prefetch distance in tiles; -1: each kernel's built-in default
 std::mutex g_ctx_mu;
 std::map<int, DeviceCtx*> g_ctx;
 
@@ -316,6 +317,8 @@ int size_class(int64_t n) {
 }
 
 }  // namespace
+
+int prefetch_tiles(int builtin) { return g_prefetch_tiles < 0 ? builtin : g_prefetch_tiles; }
 
 xs_status set_error(xs_status s) {
   g_last = s;
@@ -439,7 +442,7 @@ xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState
   a.out = d_out;
   a.mode = mode;
   a.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * K.unroll));
-  a.prefetch = g_prefetch_tiles;
+  a.prefetch = prefetch_tiles(kSumPrefetch);
   a.divisor = divisor;
   K.fn<<<(unsigned)g, K.block, K.smem, s>>>(a);
   XS_TRY_CUDA(cudaGetLastError());
@@ -462,7 +465,7 @@ xs_status launch_small_fixed(const double* d_values, int64_t n, AccState* target
   a.out = d_out;
   a.mode = 0;
   a.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * U));
-  a.prefetch = g_prefetch_tiles;
+  a.prefetch = prefetch_tiles(kSumPrefetch);
   a.divisor = 0ull;
   k_sum_small<B, U><<<(unsigned)g, B, small_smem<B>(), s>>>(a);
   XS_TRY_CUDA(cudaGetLastError());
@@ -521,7 +524,7 @@ xs_status xs_default_shape(int64_t n, int* method, int* block, int* unroll) {
 }
 
 xs_status xs_set_prefetch_tiles(int tiles) {
-  if (tiles < 0 || tiles > 64) return set_error(XS_ERR_INVALID_VALUE);
+  if (tiles < -1 || tiles > 64) return set_error(XS_ERR_INVALID_VALUE);
   g_prefetch_tiles = tiles;
   return set_error(XS_OK);
 }

@@ -139,6 +139,17 @@ __device__ __forceinline__ void sacc_add_normal(long long* __restrict__ a, unsig
   c[STRIDE] = (long long)((unsigned long long)c[STRIDE] + x1 + s1);
 }
 
+// A zero, subnormal, Inf or NaN term b that went through sacc_add_normal as if
+// it were normal: cancel that add exactly (same term, sign bit flipped), then
+// add a zero or subnormal through the general path (Inf and NaN add nothing).
+// Out of line: it runs only for such rare terms.
+template <int STRIDE>
+__device__ __noinline__ static void take_back(long long* __restrict__ a, unsigned long long b) {
+  const unsigned lo = (unsigned)b, hi = (unsigned)(b >> 32), e = (hi >> 20) & 0x7FFu;
+  sacc_add_normal<STRIDE>(a, lo, hi ^ 0x80000000u, e);
+  if (e == 0u) sacc_add(a, STRIDE, lo, hi);
+}
+
 // Per-thread state of the small-superaccumulator path: the chunks plus the
 // Inf/NaN record and what decides the sign of an exact zero.
 struct SmallThread {
@@ -171,32 +182,41 @@ struct SmallThread {
       sacc_add(acc, BLOCK, lo, hi);
     }
   }
-  // A group of U 16-byte vectors (2U terms): one test decides whether every
-  // term is normal (then the short path), else each term takes the general one.
+  // A group of U 16-byte vectors (2U terms). Every term goes through the
+  // short path for normal terms straight away; whether all of them were
+  // normal is only looked at after the last add, so no add waits for the
+  // test. A zero, subnormal, Inf or NaN term (rare) is then taken back
+  // exactly -- the short path on the same term with the sign bit flipped adds
+  // the two's complement of what it added before -- and given to the general
+  // path. Between two carry propagations a chunk so holds at most the adds of
+  // the terms seen, as without the detour.
   template <int BLOCK, int U>
   __device__ __forceinline__ void group(const ulonglong2* v) {
-    unsigned e[2 * U];
     unsigned mx = 0u;
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-      e[2 * k] = ((unsigned)(v[k].x >> 32) >> 20) & 0x7FFu;
-      e[2 * k + 1] = ((unsigned)(v[k].y >> 32) >> 20) & 0x7FFu;
-      mx = max(mx, e[2 * k] - 1u);  // e == 0 wraps to the top: not normal
-      mx = max(mx, e[2 * k + 1] - 1u);
+      const unsigned h0 = (unsigned)(v[k].x >> 32), h1 = (unsigned)(v[k].y >> 32);
+      const unsigned e0 = (h0 >> 20) & 0x7FFu, e1 = (h1 >> 20) & 0x7FFu;
+      mx = max(mx, e0 - 1u);  // e == 0 wraps to the top: not normal
+      mx = max(mx, e1 - 1u);
+      sacc_add_normal<BLOCK>(acc, (unsigned)v[k].x, h0, e0);
+      sacc_add_normal<BLOCK>(acc, (unsigned)v[k].y, h1, e1);
     }
     if (__builtin_expect(mx < 0x7FEu, 1)) {
       notnegz = 1u;
+      return;
+    }
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        sacc_add_normal<BLOCK>(acc, (unsigned)v[k].x, (unsigned)(v[k].x >> 32), e[2 * k]);
-        sacc_add_normal<BLOCK>(acc, (unsigned)v[k].y, (unsigned)(v[k].y >> 32), e[2 * k + 1]);
+    for (int k = 0; k < 2 * U; ++k) {
+      const unsigned long long b = (k & 1) ? v[k >> 1].y : v[k >> 1].x;
+      const unsigned e = ((unsigned)(b >> 32) >> 20) & 0x7FFu;
+      if (e - 1u < 0x7FEu) {
+        notnegz = 1u;
+        continue;
       }
-    } else {
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        one<BLOCK>(v[k].x);
-        one<BLOCK>(v[k].y);
-      }
+      notnegz |= (b != kNegZero) ? 1u : 0u;
+      take_back<BLOCK>(acc, b);
+      if (e == 0x7FFu) special(b);
     }
   }
   __device__ __forceinline__ unsigned flags() const {
@@ -296,29 +316,53 @@ __device__ __forceinline__ unsigned long long warp_max_ull(unsigned long long v)
 // Block reduction of the per-thread chunks without a final per-thread carry
 // propagation: chunk c of every thread (|c| < 2^63) splits into its low 32 bits
 // and its signed high part, and the high part is owed to chunk c+1. Warp w
-// handles chunks w, w + BLOCK/32, ...; lane 0 hands the two warp sums to
-// `emit(chunk, value)`, which adds them into the target accumulator (global or
-// shared). Sums stay below 2^41 in magnitude for BLOCK <= 512.
+// handles chunks w, w + BLOCK/32, ..., a batch of up to 6 at a time so their
+// shared-memory reads overlap. Each lane first sums its BLOCK/32 threads'
+// parts (low < 2^36, high of magnitude < 2^35 for BLOCK <= 512); the warp sums
+// then come from 32-bit warp reductions of 16-bit digits of those partials
+// (each digit sum stays below 2^25 in magnitude, so the reductions are exact).
+// Lane 0 hands the two sums to `emit(chunk, value)`, which adds them into the
+// target accumulator (global or shared). Sums stay below 2^41 in magnitude.
 template <int BLOCK, typename Emit>
 __device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit) {
+  static_assert(BLOCK % 32 == 0 && BLOCK <= 512, "digit sums sized for up to 16 warps");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = BLOCK / 32;
-  for (int c = warp; c < kSChunks; c += NW) {
-    long long lo = 0, hi = 0;
+  constexpr int BATCH = 6;
+  for (int c0 = warp; c0 < kSChunks; c0 += BATCH * NW) {
+    unsigned long long lo[BATCH];
+    long long hi[BATCH];
 #pragma unroll
-    for (int k = 0; k < NW; ++k) {
-      const long long v = sm[c * BLOCK + k * 32 + lane];
-      lo += v & 0xFFFFFFFFll;
-      hi += v >> 32;
+    for (int j = 0; j < BATCH; ++j) {
+      const int c = c0 + j * NW;
+      lo[j] = 0ull;
+      hi[j] = 0;
+      if (c < kSChunks) {
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+          const long long v = sm[c * BLOCK + k * 32 + lane];
+          lo[j] += (unsigned long long)(unsigned)v;
+          hi[j] += v >> 32;
+        }
+      }
     }
-    lo = warp_sum_ll(lo);
-    hi = warp_sum_ll(hi);
-    if (lane == 0) {
-      if (c == kSChunks - 1) {
-        emit(c, lo + hi * 4294967296ll);
-      } else {
-        emit(c, lo);
-        emit(c + 1, hi);
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const int c = c0 + j * NW;
+      if (c >= kSChunks) break;
+      const unsigned l0 = __reduce_add_sync(kFull, (unsigned)lo[j] & 0xFFFFu);
+      const unsigned l1 = __reduce_add_sync(kFull, (unsigned)(lo[j] >> 16));
+      const unsigned h0 = __reduce_add_sync(kFull, (unsigned)hi[j] & 0xFFFFu);
+      const int h1 = __reduce_add_sync(kFull, (int)(hi[j] >> 16));
+      if (lane == 0) {
+        const long long L = (long long)l0 + (long long)l1 * 65536ll;
+        const long long H = (long long)h0 + (long long)h1 * 65536ll;
+        if (c == kSChunks - 1) {
+          emit(c, L + H * 4294967296ll);
+        } else {
+          emit(c, L);
+          emit(c + 1, H);
+        }
       }
     }
   }

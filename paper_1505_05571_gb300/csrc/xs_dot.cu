@@ -221,7 +221,7 @@ xs_status launch_dot(const double* x, const double* y, int64_t n, double* d_out,
   d.s.out = d_out;
   d.s.mode = 0;
   d.s.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * kDotUnroll));
-  d.s.prefetch = 3;
+  d.s.prefetch = prefetch_tiles(kDotPrefetch);
   d.s.divisor = 0ull;
   d.y = kind == 0 ? y : x;
   fn<<<(unsigned)g, kDotBlock, smem, s>>>(d);

@@ -366,7 +366,7 @@ extern "C" xs_status xs_sum_f32_async(const float* d_values, int64_t n, float* d
   a.g = reinterpret_cast<AccState32*>(w->acc_f32);  // zero at rest, cleared by the last block
   a.out = d_out;
   a.carry_tiles = std::max(1, (kF32CarryInterval - 7) / (4 * kF32Unroll));
-  a.prefetch = 3;
+  a.prefetch = prefetch_tiles(kF32Prefetch);
   const long long g = std::max<long long>(1, std::min<long long>((long long)ctx->num_sms * std::max(1, occ), ntiles));
   k_sum_f32<kF32Block, kF32Unroll><<<(unsigned)g, kF32Block, smem, s>>>(a);
   XS_TRY_CUDA(cudaGetLastError());

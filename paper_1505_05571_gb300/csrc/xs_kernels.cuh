@@ -21,11 +21,16 @@ struct SumArgs {
 // Ticket epilogue: the last block to arrive finishes the sum.
 // `sc`: block shared memory the finishing warp may use as scratch (the
 // accumulators are no longer needed when the block reaches this point).
+// The block's adds into `g` are ordered before its ticket by the barrier and
+// one device-scope fence of thread 0 (the fence is cumulative over what the
+// barrier made visible to it).
 static __device__ void finish_grid(const SumArgs& a, long long* sc) {
   __shared__ unsigned s_last;
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(&a.g->ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&a.g->ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
   __syncthreads();
   if (!s_last || threadIdx.x >= 32) return;
   __threadfence();

@@ -78,3 +78,14 @@ def test_no_oracle_in_product():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".hpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.lower().replace("no oracle", ""), f
+
+
+def test_prefetch_setting_range(lib_path):
+    """The prefetch knob takes -1 (built-in distances) .. 64 and rejects the rest
+    (host-side state only, no GPU call)."""
+    from paper_1505_05571_gb300 import xsum
+    for bad in (-2, 65, 1 << 20):
+        with pytest.raises(xsum.XsError):
+            xsum.xs_set_prefetch_tiles(bad)
+    for ok in (0, 5, 64, -1):
+        xsum.xs_set_prefetch_tiles(ok)

@@ -114,6 +114,30 @@ def test_repeat_closed_form(N):
         all_shapes_equal(np.full(N, f2b(v), dtype=np.uint64), f2b(v * N))
 
 
+@pytest.mark.parametrize("every", [3, 7, 61, 997])
+def test_rare_terms_between_largest_chunk_adds(every):
+    """Same-sign terms whose significand sits at the top of a chunk (e & 31 ==
+    31, the largest high parts, so the chunks approach their bound between
+    carry propagations), with zeros and subnormals spread through them: the
+    groups holding one go through the short path, are taken back and re-added.
+    Exact sums fixed by integer arithmetic: the oracle decides."""
+    n = 3_000_017
+    rng = np.random.default_rng(every)
+    e = np.uint64(0x7DF)  # biased exponent 2015: chunk 62, shift 31
+    x = (e << np.uint64(52)) | rng.integers(0, 1 << 52, n, dtype=np.uint64)
+    sel = np.arange(every // 2, n, every)
+    rare = np.array([0, 0x8000000000000000, 1, 0x800FFFFFFFFFFFFF, 0x0008000000000000],
+                    dtype=np.uint64)
+    x[sel] = rare[rng.integers(0, rare.size, sel.size)]
+    all_shapes_equal(x, c_oracle.sum_bits(x), misalign=(0, 1))
+    # the same with one Inf and one NaN among them: only the special record decides
+    y = x.copy()
+    y[n // 3] = 0x7FF0000000000000
+    all_shapes_equal(y, 0x7FF0000000000000)
+    y[2 * n // 3] = 0xFFF8000000000321
+    all_shapes_equal(y, c_oracle.sum_bits(y))
+
+
 def test_permutation_invariance():
     x = W.cfg2a_paired(2, 0, 500_000)
     expect = c_oracle.sum_bits(x)

@@ -1,6 +1,6 @@
 """Runs one library entry point on one synthetic workload (for timing and ncu).
 
-    python -m workloads.cases <case> [--reps N]
+    python -m workloads.cases <case> [--reps N] [--prefetch TILES]
 
 Cases: sum_cfg1, mean_cfg1, large_cfg1, dot_cfg1, norm2_cfg1, f32_2e8,
 seg_cfg3_5k (5,000 segments of the config-3 length law), seg_tiny (2,000,000
@@ -77,7 +77,13 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--prefetch", type=int, default=None,
+                    help="L2 prefetch distance in tiles (library default if absent)")
     args = ap.parse_args()
+    if args.prefetch is not None:
+        from paper_1505_05571_gb300 import xsum
+
+        xsum.xs_set_prefetch_tiles(args.prefetch)
     fn, nbytes, _keep = build_case(args.case)
     fn()
     torch.cuda.synchronize()
@@ -91,7 +97,8 @@ def main():
         times.append(a.elapsed_time(b))
     times.sort()
     t = times[len(times) // 2]
-    print(f"{args.case}: {t * 1000:.1f} us, {nbytes / (t * 1e-3) / 1e9:.1f} GB/s")
+    pf = "" if args.prefetch is None else f" (prefetch {args.prefetch})"
+    print(f"{args.case}{pf}: {t * 1000:.1f} us, {nbytes / (t * 1e-3) / 1e9:.1f} GB/s")
 
 
 if __name__ == "__main__":
