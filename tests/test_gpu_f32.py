@@ -46,3 +46,21 @@ def test_repeats(N):
 def test_full_size_2e8():
     x = rand32(0, 2 * 10 ** 8, -60, 60)
     assert gpu32(x) == c_oracle.sum_f32_bits(x)
+
+
+@pytest.mark.parametrize("every", [3, 29, 1001])
+def test_rare_terms_between_largest_slot_adds(every):
+    """Same-sign floats at the top of a slot (e & 31 == 31: the largest adds,
+    so slots approach their bound between propagations) with zeros and
+    subnormals spread through them: groups holding one are taken back and
+    re-added."""
+    n = 4_000_037
+    rng = np.random.default_rng(every)
+    x = (np.uint32(223) << np.uint32(23)) | rng.integers(0, 1 << 23, n, dtype=np.uint32)
+    sel = np.arange(every // 2, n, every)
+    rare = np.array([0, 0x80000000, 1, 0x807FFFFF, 0x00400000], dtype=np.uint32)
+    x[sel] = rare[rng.integers(0, rare.size, sel.size)]
+    for mis in (0, 1, 3):
+        assert gpu32(x, mis) == c_oracle.sum_f32_bits(x)
+    x[n // 2] = 0xFF800000
+    assert gpu32(x) == 0xFF800000

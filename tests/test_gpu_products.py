@@ -67,3 +67,26 @@ def test_full_size_norm_and_dot():
     y = W.cfg1_band(1, 0, n)
     assert gpu_norm2(x) == products.norm2_bits(x)
     assert gpu_dot(x, y) == products.dot_bits(x, y)
+
+
+def test_products_underflowing_and_overflowing_in_runs():
+    """Products that underflow to zero or a subnormal, or overflow to Inf, in
+    every group position: each is taken back from the short path and re-added
+    by the general one; the sum must stay the oracle's."""
+    n = 1_000_003
+    rng = np.random.default_rng(11)
+    x = W.cfg1_band(11, 0, n).copy()
+    y = W.cfg1_band(12, 0, n).copy()
+    tiny = np.array([0x0010000000000000, 0x8000000000000001, 0x3CB0000000000000], dtype=np.uint64)
+    sel = np.arange(5, n, 13)
+    x[sel] = tiny[rng.integers(0, tiny.size, sel.size)]
+    # 2^-53, 2^-2, 0.75: products underflow to zero or land on subnormals
+    ys = np.array([0x3CA0000000000000, 0x3FD0000000000000, 0x3FE8000000000000], dtype=np.uint64)
+    y[sel] = ys[rng.integers(0, ys.size, sel.size)]
+    assert gpu_dot(x, y) == products.dot_bits(x, y)
+    assert gpu_dot(x, y, 1, 0) == products.dot_bits(x, y)
+    big = x.copy()
+    big[7] = np.uint64(0x7FE0000000000000)
+    yb = y.copy()
+    yb[7] = np.uint64(0x7FE0000000000000)  # overflows to +Inf
+    assert gpu_dot(big, yb) == products.dot_bits(big, yb) == 0x7FF0000000000000
