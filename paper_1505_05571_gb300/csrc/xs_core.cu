@@ -81,20 +81,20 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   while (t < nfull) {
     if (tid == 0 && a.prefetch > 0) prefetch_tile<BLOCK, UNROLL>(sp, t + (a.prefetch + 1) * G, ntiles);
     if (t + G < nfull) load_full<BLOCK, UNROLL>(sp, t + G, tid, B);
-    T.group<BLOCK, UNROLL>(A);
+    T.group_spec<BLOCK, UNROLL>(A);
     tick();
     t += G;
     if (t >= nfull) break;
     if (tid == 0 && a.prefetch > 0) prefetch_tile<BLOCK, UNROLL>(sp, t + (a.prefetch + 1) * G, ntiles);
     if (t + G < nfull) load_full<BLOCK, UNROLL>(sp, t + G, tid, A);
-    T.group<BLOCK, UNROLL>(B);
+    T.group_spec<BLOCK, UNROLL>(B);
     tick();
     t += G;
   }
   // The ragged last tile (padded with -0, which adds nothing).
   if (t == nfull && nfull < ntiles) {
     load_tile<BLOCK, UNROLL>(sp, t, tid, A);
-    T.group<BLOCK, UNROLL>(A);
+    T.group_spec<BLOCK, UNROLL>(A);
   }
   __syncthreads();
   unsigned f = T.flags();
