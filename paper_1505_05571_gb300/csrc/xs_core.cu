@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   // The ragged last tile (padded with -0, which adds nothing).
   if (t == nfull && nfull < ntiles) {
     load_tile<BLOCK, UNROLL>(sp, t, tid, A);
-    T.group_spec<BLOCK, UNROLL>(A);
+    T.group_spec<BLOCK, UNROLL>(A);  // the -0 padding is taken back: once per launch
   }
   __syncthreads();
   unsigned f = T.flags();

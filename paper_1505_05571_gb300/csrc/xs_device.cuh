@@ -217,9 +217,8 @@ struct SmallThread {
   // exactly -- the short path on the same term with the sign bit flipped adds
   // the two's complement of what it added before -- and given to the general
   // path. Between two carry propagations a chunk so holds at most the adds of
-  // the terms seen, as without the detour. Measured on GB300: faster in the
-  // single-array kernel (5 %), slower inside the segmented kernel (4 %), so
-  // each kernel takes the form that suits it.
+  // the terms seen, as without the detour. Groups padded with -0 (the ragged
+  // end of a range) take the test-first form above instead.
   template <int BLOCK, int U>
   __device__ __forceinline__ void group_spec(const ulonglong2* v) {
     unsigned mx = 0u;
@@ -312,11 +311,11 @@ __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x
   while (g < nfull) {
     prefetch(g + kAhead + 1);
     if (g + 1 < nfull) load_full(g + 1, B);
-    T.group<BLOCK, UNROLL>(A);
+    T.group_spec<BLOCK, UNROLL>(A);
     if (++g >= nfull) break;
     prefetch(g + kAhead + 1);
     if (g + 1 < nfull) load_full(g + 1, A);
-    T.group<BLOCK, UNROLL>(B);
+    T.group_spec<BLOCK, UNROLL>(B);
     ++g;
   }
   if (nfull * gsz < npairs) {
@@ -325,7 +324,7 @@ __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x
       const long long k = nfull * gsz + (long long)u * nthr + r;
       A[u] = k < npairs ? ld_stream(xv + k) : make_ulonglong2(kNegZero, kNegZero);
     }
-    T.group<BLOCK, UNROLL>(A);
+    T.group<BLOCK, UNROLL>(A);  // the -0 padding is not normal: test first
   }
 }
 

@@ -168,8 +168,23 @@ __global__ void __launch_bounds__(kPrepThreads) k_seg_fill(SegArgs a) {
   }
 }
 
+constexpr int kPhase1Ahead = 6;  // groups of a tile prefetched before the block starts it
+
+// L2 prefetch of the 16-byte-aligned part of [p, q), in pieces of at most 64 KB.
+__device__ __forceinline__ void prefetch_range(const unsigned long long* p,
+                                               const unsigned long long* q) {
+  uintptr_t b0 = ((uintptr_t)p + 15u) & ~(uintptr_t)15u;
+  const uintptr_t b1 = (uintptr_t)q & ~(uintptr_t)15u;
+  while (b0 < b1) {
+    const uintptr_t n = min(b1 - b0, (uintptr_t)65536u);
+    prefetch_l2((const void*)b0, (unsigned)n);
+    b0 += n;
+  }
+}
+
 template <int BLOCK, int UNROLL>
 __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
+  static_assert(BLOCK >= 64, "warp 1 claims and prefetches the next tile");
   extern __shared__ __align__(16) long long smem_seg[];
   __shared__ long long bsum[kSChunks];
   __shared__ long long s_item;
@@ -181,10 +196,24 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
   T.acc = smem_seg + tid;
   const long long ntiles = (long long)a.counters[0];
   const long long nshort = (long long)a.counters[1];
+  const unsigned long long* xb_all = reinterpret_cast<const unsigned long long*>(a.x);
 
   // ---- phase 1: tiles of long segments, one block each ----
+  // The next tile is claimed while the block merges the current one, and its
+  // start is prefetched into L2 before the block moves on, so neither the
+  // claim nor a tile's first loads wait behind the previous merge.
+  // segment of tile t: from the table, else the last s with tile_start[s] <= t
+  auto segment_of = [&](long long t) -> long long {
+    if (ntiles <= a.tile_cap) return a.tile_seg[t];
+    long long lo_s = 0, hi_s = a.nseg;  // invariant: tile_start[lo_s] <= t < tile_start[hi_s]
+    while (hi_s - lo_s > 1) {
+      const long long mid = (lo_s + hi_s) >> 1;
+      if (a.tile_start[mid] <= t) lo_s = mid; else hi_s = mid;
+    }
+    return lo_s;
+  };
+  if (tid == 0) s_item = (long long)atomicAdd(&a.counters[2], 1ull);
   for (;;) {
-    if (tid == 0) s_item = (long long)atomicAdd(&a.counters[2], 1ull);
     if (tid < kSChunks) bsum[tid] = 0;
     if (tid == 0) {
       s_flags = 0u;
@@ -193,18 +222,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     __syncthreads();
     const long long t = s_item;
     if (t >= ntiles) break;
-    // segment of tile t: from the table, else the last s with tile_start[s] <= t
-    long long s;
-    if (ntiles <= a.tile_cap) {
-      s = a.tile_seg[t];
-    } else {
-      long long lo_s = 0, hi_s = a.nseg;  // invariant: tile_start[lo_s] <= t < tile_start[hi_s]
-      while (hi_s - lo_s > 1) {
-        const long long mid = (lo_s + hi_s) >> 1;
-        if (a.tile_start[mid] <= t) lo_s = mid; else hi_s = mid;
-      }
-      s = lo_s;
-    }
+    const long long s = segment_of(t);
     const long long first_tile = a.tile_start[s];
     const long long seg_tiles = a.tile_start[s + 1] - first_tile;
     const long long seg_lo = a.off[s], seg_hi = a.off[s + 1];
@@ -213,7 +231,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
     T.reset();
     accumulate_range<BLOCK, UNROLL, true>(T, a.x, lo, hi, tid, BLOCK);
-    __syncthreads();
+    __syncthreads();  // every thread has read s_item
+    if (tid == 32) s_item = (long long)atomicAdd(&a.counters[2], 1ull);
     unsigned f = __reduce_or_sync(kFull, T.flags());
     const unsigned long long k = warp_max_ull(T.nkey);
     if (lane == 0) {
@@ -265,6 +284,16 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
         if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
       }
     }
+    if (tid == 32) {  // the first groups of the next tile, into L2 (beside warp 0's rounding)
+      const long long tn = s_item;
+      if (tn < ntiles) {
+        const long long sn = segment_of(tn);
+        const long long nlo = a.off[sn] + (tn - a.tile_start[sn]) * a.tile_elems;
+        const long long nhi = min(min(nlo + a.tile_elems, a.off[sn + 1]),
+                                  nlo + (long long)kPhase1Ahead * 2 * UNROLL * BLOCK);
+        prefetch_range(xb_all + nlo, xb_all + nhi);
+      }
+    }
     __syncthreads();
   }
 
@@ -284,7 +313,15 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
       mlo = a.off[ms];
       mhi = a.off[ms + 1];
     }
+    // segment j of the claim into L2 (warp-uniform call: shuffles)
+    auto prefetch_seg = [&](int j) {
+      const long long plo = __shfl_sync(kFull, mlo, j & 31), phi = __shfl_sync(kFull, mhi, j & 31);
+      if (lane == 0 && j < cnt) prefetch_range(xb + plo, xb + phi);
+    };
+    prefetch_seg(0);
+    prefetch_seg(1);
     for (int q = 0; q < cnt; ++q) {
+    prefetch_seg(q + 2);
     const long long s = __shfl_sync(kFull, ms, q);
     const long long lo = __shfl_sync(kFull, mlo, q), hi = __shfl_sync(kFull, mhi, q);
     const long long L = hi - lo;
