@@ -151,17 +151,24 @@ __device__ __noinline__ static void take_back(long long* __restrict__ a, unsigne
 }
 
 // Per-thread state of the small-superaccumulator path: the chunks plus the
-// Inf/NaN record and what decides the sign of an exact zero.
+// Inf/NaN record and what decides the sign of an exact zero. With TRACK, the
+// range of positional exponents max(e, 1) of the finite nonzero terms seen
+// ([emin, emax], empty while emax < emin) is kept as well, so a merge can
+// read, and clear, only the chunks those terms touched (Discussion: low
+// fixed cost when few chunks are in use).
 struct SmallThread {
   long long* acc;  // this thread's chunks, stride BLOCK
   unsigned notnegz = 0u;  // saw a term other than -0
   unsigned sflags = 0u;
   unsigned long long nkey = 0ull;
+  unsigned emin = 0x7FFu, emax = 0u;
 
   __device__ __forceinline__ void reset() {
     notnegz = 0u;
     sflags = 0u;
     nkey = 0ull;
+    emin = 0x7FFu;
+    emax = 0u;
   }
   __device__ __forceinline__ void special(unsigned long long b) {
     if (b & kMantMask) {
@@ -171,11 +178,20 @@ struct SmallThread {
       sflags |= (b >> 63) ? kFlagNegInf : kFlagPosInf;
     }
   }
+  __device__ __forceinline__ void track(unsigned long long b) {
+    const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+    if (e != 0x7FFu && (b << 1) != 0ull) {  // finite and nonzero
+      const unsigned ee = e ? e : 1u;
+      emin = min(emin, ee);
+      emax = max(emax, ee);
+    }
+  }
   // Any term: zeros, subnormals and Inf/NaN included.
-  template <int BLOCK>
+  template <int BLOCK, bool TRACK = false>
   __device__ __forceinline__ void one(unsigned long long b) {
     const unsigned lo = (unsigned)b, hi = (unsigned)(b >> 32);
     notnegz |= (b != kNegZero) ? 1u : 0u;
+    if (TRACK) track(b);
     if (((hi >> 20) & 0x7FFu) == 0x7FFu) {
       special(b);
     } else {
@@ -184,19 +200,24 @@ struct SmallThread {
   }
   // A group of U 16-byte vectors (2U terms): one test decides whether every
   // term is normal (then the short path), else each term takes the general one.
-  template <int BLOCK, int U>
+  template <int BLOCK, int U, bool TRACK = false>
   __device__ __forceinline__ void group(const ulonglong2* v) {
     unsigned e[2 * U];
-    unsigned mx = 0u;
+    unsigned mx = 0u, mn = 0x7FFu;
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       e[2 * k] = ((unsigned)(v[k].x >> 32) >> 20) & 0x7FFu;
       e[2 * k + 1] = ((unsigned)(v[k].y >> 32) >> 20) & 0x7FFu;
       mx = max(mx, e[2 * k] - 1u);  // e == 0 wraps to the top: not normal
       mx = max(mx, e[2 * k + 1] - 1u);
+      if (TRACK) mn = min(mn, min(e[2 * k], e[2 * k + 1]));
     }
     if (__builtin_expect(mx < 0x7FEu, 1)) {
       notnegz = 1u;
+      if (TRACK) {
+        emin = min(emin, mn);
+        emax = max(emax, mx + 1u);
+      }
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         sacc_add_normal<BLOCK>(acc, (unsigned)v[k].x, (unsigned)(v[k].x >> 32), e[2 * k]);
@@ -205,8 +226,8 @@ struct SmallThread {
     } else {
 #pragma unroll
       for (int k = 0; k < U; ++k) {
-        one<BLOCK>(v[k].x);
-        one<BLOCK>(v[k].y);
+        one<BLOCK, TRACK>(v[k].x);
+        one<BLOCK, TRACK>(v[k].y);
       }
     }
   }
@@ -219,26 +240,32 @@ struct SmallThread {
   // path. Between two carry propagations a chunk so holds at most the adds of
   // the terms seen, as without the detour. Groups padded with -0 (the ragged
   // end of a range) take the test-first form above instead.
-  template <int BLOCK, int U>
+  template <int BLOCK, int U, bool TRACK = false>
   __device__ __forceinline__ void group_spec(const ulonglong2* v) {
-    unsigned mx = 0u;
+    unsigned mx = 0u, mn = 0x7FFu;
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       const unsigned h0 = (unsigned)(v[k].x >> 32), h1 = (unsigned)(v[k].y >> 32);
       const unsigned e0 = (h0 >> 20) & 0x7FFu, e1 = (h1 >> 20) & 0x7FFu;
       mx = max(mx, e0 - 1u);  // e == 0 wraps to the top: not normal
       mx = max(mx, e1 - 1u);
+      if (TRACK) mn = min(mn, min(e0, e1));
       sacc_add_normal<BLOCK>(acc, (unsigned)v[k].x, h0, e0);
       sacc_add_normal<BLOCK>(acc, (unsigned)v[k].y, h1, e1);
     }
     if (__builtin_expect(mx < 0x7FEu, 1)) {
       notnegz = 1u;
+      if (TRACK) {
+        emin = min(emin, mn);
+        emax = max(emax, mx + 1u);
+      }
       return;
     }
 #pragma unroll
     for (int k = 0; k < 2 * U; ++k) {
       const unsigned long long b = (k & 1) ? v[k >> 1].y : v[k >> 1].x;
       const unsigned e = ((unsigned)(b >> 32) >> 20) & 0x7FFu;
+      if (TRACK) track(b);
       if (e - 1u < 0x7FEu) {
         notnegz = 1u;
         continue;
@@ -274,17 +301,17 @@ __device__ __forceinline__ void sacc_propagate(long long* __restrict__ a, int st
 // added), the ragged last group is padded with -0. One unaligned head and one
 // odd tail element go to ranks 0 and nthr-1. With PREFETCH, rank 0 prefetches
 // the range into L2 a few groups ahead.
-template <int BLOCK, int UNROLL, bool PREFETCH>
+template <int BLOCK, int UNROLL, bool PREFETCH, bool TRACK = false>
 __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x, long long lo,
                                                  long long hi, int r, int nthr) {
   const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(x);
   long long p = lo;
   if (p < hi && (((uintptr_t)(x + p)) & 15u) != 0u) {
-    if (r == 0) T.one<BLOCK>(xb[p]);
+    if (r == 0) T.one<BLOCK, TRACK>(xb[p]);
     ++p;
   }
   if (((hi - p) & 1) != 0 && p < hi) {
-    if (r == nthr - 1) T.one<BLOCK>(xb[hi - 1]);
+    if (r == nthr - 1) T.one<BLOCK, TRACK>(xb[hi - 1]);
     --hi;
   }
   const long long npairs = (hi - p) >> 1;
@@ -311,11 +338,11 @@ __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x
   while (g < nfull) {
     prefetch(g + kAhead + 1);
     if (g + 1 < nfull) load_full(g + 1, B);
-    T.group_spec<BLOCK, UNROLL>(A);
+    T.group_spec<BLOCK, UNROLL, TRACK>(A);
     if (++g >= nfull) break;
     prefetch(g + kAhead + 1);
     if (g + 1 < nfull) load_full(g + 1, A);
-    T.group_spec<BLOCK, UNROLL>(B);
+    T.group_spec<BLOCK, UNROLL, TRACK>(B);
     ++g;
   }
   if (nfull * gsz < npairs) {
@@ -324,7 +351,7 @@ __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x
       const long long k = nfull * gsz + (long long)u * nthr + r;
       A[u] = k < npairs ? ld_stream(xv + k) : make_ulonglong2(kNegZero, kNegZero);
     }
-    T.group<BLOCK, UNROLL>(A);  // the -0 padding is not normal: test first
+    T.group<BLOCK, UNROLL, TRACK>(A);  // the -0 padding is not normal: test first
   }
 }
 
@@ -352,13 +379,15 @@ __device__ __forceinline__ unsigned long long warp_max_ull(unsigned long long v)
 // (each digit sum stays below 2^25 in magnitude, so the reductions are exact).
 // Lane 0 hands the two sums to `emit(chunk, value)`, which adds them into the
 // target accumulator (global or shared). Sums stay below 2^41 in magnitude.
+// Only chunks c_lo..c_hi are read (the others must be zero in every thread).
 template <int BLOCK, typename Emit>
-__device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit) {
+__device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit, int c_lo = 0,
+                                                 int c_hi = kSChunks - 1) {
   static_assert(BLOCK % 32 == 0 && BLOCK <= 512, "digit sums sized for up to 16 warps");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = BLOCK / 32;
   constexpr int BATCH = 6;
-  for (int c0 = warp; c0 < kSChunks; c0 += BATCH * NW) {
+  for (int c0 = c_lo + warp; c0 <= c_hi; c0 += BATCH * NW) {
     unsigned long long lo[BATCH];
     long long hi[BATCH];
 #pragma unroll
@@ -366,7 +395,7 @@ __device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit)
       const int c = c0 + j * NW;
       lo[j] = 0ull;
       hi[j] = 0;
-      if (c < kSChunks) {
+      if (c <= c_hi) {
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
           const long long v = sm[c * BLOCK + k * 32 + lane];
@@ -378,7 +407,7 @@ __device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit)
 #pragma unroll
     for (int j = 0; j < BATCH; ++j) {
       const int c = c0 + j * NW;
-      if (c >= kSChunks) break;
+      if (c > c_hi) break;
       const unsigned l0 = __reduce_add_sync(kFull, (unsigned)lo[j] & 0xFFFFu);
       const unsigned l1 = __reduce_add_sync(kFull, (unsigned)(lo[j] >> 16));
       const unsigned h0 = __reduce_add_sync(kFull, (unsigned)hi[j] & 0xFFFFu);

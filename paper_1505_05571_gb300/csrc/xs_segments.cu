@@ -191,9 +191,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
   __shared__ unsigned s_flags;
   __shared__ unsigned long long s_nkey;
   __shared__ unsigned s_last;
+  __shared__ unsigned s_emin, s_emax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   SmallThread T;
   T.acc = smem_seg + tid;
+  // The accumulators are cleared once; every merge clears again the chunks it
+  // read (the window of chunks the terms touched), and the rounding scratch
+  // lives outside them, so they are zero whenever a new sum starts.
+  for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
   const long long ntiles = (long long)a.counters[0];
   const long long nshort = (long long)a.counters[1];
   const unsigned long long* xb_all = reinterpret_cast<const unsigned long long*>(a.x);
@@ -212,27 +217,47 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     }
     return lo_s;
   };
-  if (tid == 0) s_item = (long long)atomicAdd(&a.counters[2], 1ull);
+  // where tile t lies: its segment, element range and the segment's tile count
+  __shared__ long long s_meta[4];
+  auto describe = [&](long long t) {
+    const long long sg = segment_of(t);
+    const long long ft = a.tile_start[sg];
+    const long long tl = a.off[sg] + (t - ft) * a.tile_elems;
+    s_meta[0] = sg;
+    s_meta[1] = tl;
+    s_meta[2] = min(tl + a.tile_elems, a.off[sg + 1]);
+    s_meta[3] = a.tile_start[sg + 1] - ft;
+  };
+  if (tid == 0) {
+    s_item = (long long)atomicAdd(&a.counters[2], 1ull);
+    if (s_item < ntiles) describe(s_item);
+  }
   for (;;) {
     if (tid < kSChunks) bsum[tid] = 0;
     if (tid == 0) {
       s_flags = 0u;
       s_nkey = 0ull;
+      s_emin = 0x7FFu;
+      s_emax = 0u;
     }
     __syncthreads();
     const long long t = s_item;
     if (t >= ntiles) break;
-    const long long s = segment_of(t);
-    const long long first_tile = a.tile_start[s];
-    const long long seg_tiles = a.tile_start[s + 1] - first_tile;
-    const long long seg_lo = a.off[s], seg_hi = a.off[s + 1];
-    const long long lo = seg_lo + (t - first_tile) * a.tile_elems;
-    const long long hi = min(lo + a.tile_elems, seg_hi);
-    for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
+    const long long s = s_meta[0], lo = s_meta[1], hi = s_meta[2], seg_tiles = s_meta[3];
     T.reset();
-    accumulate_range<BLOCK, UNROLL, true>(T, a.x, lo, hi, tid, BLOCK);
-    __syncthreads();  // every thread has read s_item
+    accumulate_range<BLOCK, UNROLL, true, true>(T, a.x, lo, hi, tid, BLOCK);
+    {
+      const unsigned wmin = __reduce_min_sync(kFull, T.emin);
+      const unsigned wmax = __reduce_max_sync(kFull, T.emax);
+      if (lane == 0 && wmax >= wmin) {
+        atomicMin(&s_emin, wmin);
+        atomicMax(&s_emax, wmax);
+      }
+    }
+    __syncthreads();  // every thread has read s_item; the window is complete
     if (tid == 32) s_item = (long long)atomicAdd(&a.counters[2], 1ull);
+    const int cmin = (int)(s_emin >> kLowExpBits);
+    const int cmax = s_emax >= s_emin ? (int)(s_emax >> kLowExpBits) + 1 : cmin - 1;  // empty
     unsigned f = __reduce_or_sync(kFull, T.flags());
     const unsigned long long k = warp_max_ull(T.nkey);
     if (lane == 0) {
@@ -242,14 +267,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     if (seg_tiles == 1) {
       block_chunk_sums<BLOCK>(smem_seg, [&](int c, long long v) {
         atomicAdd(reinterpret_cast<unsigned long long*>(bsum + c), (unsigned long long)v);
-      });
+      }, cmin, cmax);
       __syncthreads();
+      for (int c = cmin; c <= cmax; ++c) T.acc[c * BLOCK] = 0;
       if (warp == 0) {
-        const unsigned bits = 0u;
-        (void)bits;
-        const unsigned long long r = warp_round(bsum[lane], bsum[lane + 32],
-                                                lane < 3 ? bsum[lane + 64] : 0,
-                                                s_flags | kFlagAny, s_nkey, smem_seg, 32);
+        const long long v0 = bsum[lane], v1 = bsum[lane + 32], v2 = lane < 3 ? bsum[lane + 64] : 0;
+        __syncwarp();  // bsum is the rounding scratch from here on
+        const unsigned long long r = warp_round(v0, v1, v2, s_flags | kFlagAny, s_nkey, bsum, 32);
         if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
       }
     } else {
@@ -257,8 +281,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
       unsigned long long* gc = reinterpret_cast<unsigned long long*>(g->chunk);
       block_chunk_sums<BLOCK>(smem_seg, [&](int c, long long v) {
         if (v != 0) atomicAdd(gc + c, (unsigned long long)v);
-      });
+      }, cmin, cmax);
       __syncthreads();
+      for (int c = cmin; c <= cmax; ++c) T.acc[c * BLOCK] = 0;
       if (tid == 0) {
         if (s_flags) atomicOr(&g->flags, s_flags);
         if (s_nkey) atomicMax(&g->nan_key, s_nkey);
@@ -280,18 +305,16 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
         }
         fl = __shfl_sync(kFull, fl, 0);
         key = __shfl_sync(kFull, key, 0);
-        const unsigned long long r = warp_round(v0, v1, v2, fl | kFlagAny, key, smem_seg, 32);
+        const unsigned long long r = warp_round(v0, v1, v2, fl | kFlagAny, key, bsum, 32);
         if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
       }
     }
-    if (tid == 32) {  // the first groups of the next tile, into L2 (beside warp 0's rounding)
-      const long long tn = s_item;
+    if (tid == 32) {  // the next tile: where it lies, and its first groups into L2
+      const long long tn = s_item;  // beside warp 0's rounding
       if (tn < ntiles) {
-        const long long sn = segment_of(tn);
-        const long long nlo = a.off[sn] + (tn - a.tile_start[sn]) * a.tile_elems;
-        const long long nhi = min(min(nlo + a.tile_elems, a.off[sn + 1]),
-                                  nlo + (long long)kPhase1Ahead * 2 * UNROLL * BLOCK);
-        prefetch_range(xb_all + nlo, xb_all + nhi);
+        describe(tn);
+        prefetch_range(xb_all + s_meta[1],
+                       xb_all + min(s_meta[2], s_meta[1] + (long long)kPhase1Ahead * 2 * UNROLL * BLOCK));
       }
     }
     __syncthreads();
@@ -361,13 +384,15 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
       }
       cmin = __reduce_min_sync(kFull, mn);
       cmax = __reduce_max_sync(kFull, mx);
-      for (int c = cmin; c <= cmax; ++c) T.acc[c * BLOCK] = 0;
-      // zeros outside the window add 0 to chunks that are never read
+      // zeros add 0 to chunks that stay zero
 #pragma unroll
       for (int k = 0; k < 4; ++k) T.one<BLOCK>(v[k]);
     } else {
-      for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
-      accumulate_range<BLOCK, 2, false>(T, a.x, lo, hi, lane, 32);
+      accumulate_range<BLOCK, 2, false, true>(T, a.x, lo, hi, lane, 32);
+      const unsigned wmin = __reduce_min_sync(kFull, T.emin);
+      const unsigned wmax = __reduce_max_sync(kFull, T.emax);
+      cmin = (int)(wmin >> kLowExpBits);
+      cmax = wmax >= wmin ? (int)(wmax >> kLowExpBits) + 1 : cmin - 1;  // empty
     }
     __syncwarp();
     // lane L gathers chunks L, L+32, L+64 of the warp's 32 accumulators (only
@@ -402,9 +427,15 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     const long long v2 = lane < 3 ? lo2 + in2 + top_hi * 4294967296ll : 0;
     const unsigned f = __reduce_or_sync(kFull, T.flags()) | kFlagAny;
     const unsigned long long key = warp_max_ull(T.nkey);
-    __syncwarp();  // every lane's gather is done: column 0 of the warp is scratch now
+    __syncwarp();  // every lane's gather is done
+    for (int c = cmin; c <= cmax; ++c) T.acc[c * BLOCK] = 0;
+    __syncwarp();  // chunks 0..2 of the warp's threads are the rounding scratch now
     const unsigned long long r = warp_round(v0, v1, v2, f, key, smem_seg + warp * 32, BLOCK);
     if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
+    __syncwarp();
+    T.acc[0] = 0;
+    T.acc[BLOCK] = 0;
+    if (lane < 3) T.acc[2 * BLOCK] = 0;
     __syncwarp();
     }
   }
