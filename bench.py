@@ -46,15 +46,17 @@ def read_peaks():
 # Source regions that define each profiled kernel: the shared device header
 # plus the kernel's own section of its translation unit.
 PREFETCH_DEFAULTS = ("xs_host.hpp", "int prefetch_tiles(int builtin);", "inline cudaStream_t as_stream")
+DEVICE_BLOCKS = ("xs_device.cuh", None, None)
 KERNEL_SOURCES = {
-    "k_sum_small": [("xs_kernels.cuh", None, None),
+    "k_sum_small": [DEVICE_BLOCKS, ("xs_kernels.cuh", None, None),
                     ("xs_core.cu", "__device__ __forceinline__ void load_tile(",
                      "// Large superaccumulator kernel"), PREFETCH_DEFAULTS],
-    "k_sum_large": [("xs_kernels.cuh", None, None),
+    "k_sum_large": [DEVICE_BLOCKS, ("xs_kernels.cuh", None, None),
                     ("xs_core.cu", "// Large superaccumulator kernel", "// Accumulator-handle kernels")],
-    "k_seg_main": [("xs_segments.cu", "struct SegArgs {", "namespace {")],
-    "k_dot_small": [("xs_kernels.cuh", None, None), ("xs_dot.cu", None, None), PREFETCH_DEFAULTS],
-    "k_sum_f32": [("xs_f32.cu", None, None), PREFETCH_DEFAULTS],
+    "k_seg_main": [DEVICE_BLOCKS, ("xs_segments.cu", None, None)],
+    "k_dot_small": [DEVICE_BLOCKS, ("xs_kernels.cuh", None, None), ("xs_dot.cu", None, None),
+                    PREFETCH_DEFAULTS],
+    "k_sum_f32": [DEVICE_BLOCKS, ("xs_f32.cu", None, None), PREFETCH_DEFAULTS],
 }
 
 
@@ -183,11 +185,45 @@ def cpu_oracle_run(seconds_target: float = 15.0):
     for _ in range(reps):
         c_oracle.sum_bits(x)
     dt = time.perf_counter() - t0
-    del np
-    return {"value": round(8.0 * chunk * reps / dt / 1e9, 4), "unit": "GB/s", "cores": 1,
+    line = {"value": round(8.0 * chunk * reps / dt / 1e9, 4), "unit": "GB/s", "cores": 1,
             "kind": "oracle",
             "sample": f"first {chunk:.0e} elements of the workload, summed {reps} times "
-                      f"({dt:.1f} s, single-threaded plain-C big-integer oracle)"}
+                      f"({dt:.1f} s, single-threaded plain-C big-integer oracle)",
+            "host": host_cpu()}
+    # every host core: the oracle's OpenMP entry over one independent slice per thread
+    threads = max(1, c_oracle.max_threads())
+    xs = np.tile(x, threads)
+    off = np.arange(threads + 1, dtype=np.int64) * chunk
+    t0 = time.perf_counter()
+    c_oracle.segment_sums_bits(xs, off)
+    per = time.perf_counter() - t0
+    reps_all = max(1, min(50, int(seconds_target / 2 / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    for _ in range(reps_all):
+        c_oracle.segment_sums_bits(xs, off)
+    dt_all = time.perf_counter() - t0
+    line["all_cores"] = {
+        "value": round(8.0 * chunk * threads * reps_all / dt_all / 1e9, 4), "unit": "GB/s",
+        "cores": threads,
+        "sample": f"{threads} slices of {chunk:.0e} elements (copies of the same sample), one per "
+                  f"OpenMP thread, {reps_all} passes ({dt_all:.1f} s)"}
+    return line
+
+
+def host_cpu() -> str:
+    """Model name and logical CPU count of this host (from lscpu when present)."""
+    import platform
+    import subprocess
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return f"{model}, {os.cpu_count()} logical CPUs"
 
 
 def run_reference(args):
