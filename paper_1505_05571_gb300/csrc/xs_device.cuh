@@ -318,7 +318,7 @@ __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x
   const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(x + p);
   const long long gsz = (long long)UNROLL * nthr;  // pairs per group
   const long long nfull = npairs / gsz;
-  constexpr int kAhead = 6;  // groups prefetched ahead
+  constexpr int kAhead = UNROLL >= 24 ? 1 : 24 / UNROLL;  // groups prefetched ahead (~24 loads per thread)
   auto prefetch = [&](long long g) {
     if (PREFETCH && r == 0 && g < nfull + 1) {
       const long long first = g * gsz;

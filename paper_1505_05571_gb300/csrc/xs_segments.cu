@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_seg_fill(SegArgs a) {
   }
 }
 
-constexpr int kPhase1Ahead = 6;  // groups of a tile prefetched before the block starts it
+constexpr int kPhase1Ahead = 48;  // values per thread of a tile prefetched before the block starts it
 
 // L2 prefetch of the 16-byte-aligned part of [p, q), in pieces of at most 64 KB.
 __device__ __forceinline__ void prefetch_range(const unsigned long long* p,
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
       if (tn < ntiles) {
         describe(tn);
         prefetch_range(xb_all + s_meta[1],
-                       xb_all + min(s_meta[2], s_meta[1] + (long long)kPhase1Ahead * 2 * UNROLL * BLOCK));
+                       xb_all + min(s_meta[2], s_meta[1] + (long long)kPhase1Ahead * BLOCK));
       }
     }
     __syncthreads();
