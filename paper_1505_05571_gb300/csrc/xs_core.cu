@@ -403,7 +403,9 @@ Workspace* workspace(DeviceCtx* ctx, cudaStream_t s, xs_status* st) {
     w->acc_host = w->acc + 1;
     w->acc_f32 = w->acc + 2;
     w->d_out = reinterpret_cast<double*>(w->acc + 3);
-    e = cudaMallocHost(&w->h_out, sizeof(double));
+    // mapped: the finishing warp stores the result straight into host memory
+    e = cudaHostAlloc(&w->h_out, sizeof(double), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&w->h_out_dev), w->h_out, 0);
   }
   if (e != cudaSuccess) {
     if (w->acc) cudaFree(w->acc);
@@ -593,11 +595,10 @@ xs_status xs_sum_ex(const double* d_values, int64_t n, void* stream, double* h_o
   if (!ctx) return st;
   Workspace* w = workspace(ctx, s, &st);
   if (!w) return st;
-  st = launch_sum(ctx, d_values, n, w->acc, w->d_out, 0, default_shape(ctx, n), 0, s);
+  st = launch_sum(ctx, d_values, n, w->acc, w->h_out_dev, 0, default_shape(ctx, n), 0, s);
   if (st != XS_OK) return st;
-  XS_TRY_CUDA(cudaMemcpyAsync(w->h_out, w->d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
   XS_TRY_CUDA(cudaStreamSynchronize(s));
-  *h_out = *w->h_out;
+  *h_out = *static_cast<volatile double*>(w->h_out);
   return set_error(XS_OK);
 }
 
@@ -654,11 +655,10 @@ xs_status xs_sum_host(const double* h_values, int64_t n, double* h_out, void* st
     XS_TRY_CUDA(cudaEventRecord(w->free_[slot], s));
     done += m;
   }
-  k_acc_round<<<1, 32, 0, s>>>(w->acc_host, w->d_out, 0ull);
+  k_acc_round<<<1, 32, 0, s>>>(w->acc_host, w->h_out_dev, 0ull);
   XS_TRY_CUDA(cudaGetLastError());
-  XS_TRY_CUDA(cudaMemcpyAsync(w->h_out, w->d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
   XS_TRY_CUDA(cudaStreamSynchronize(s));
-  *h_out = *w->h_out;
+  *h_out = *static_cast<volatile double*>(w->h_out);
   return set_error(XS_OK);
 }
 

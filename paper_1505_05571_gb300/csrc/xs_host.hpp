@@ -34,7 +34,8 @@ struct Workspace {
   AccState* acc_host = nullptr;   // accumulator of xs_sum_host
   AccState* acc_f32 = nullptr;    // grid accumulator of the FP32 sum (its smaller layout)
   double* d_out = nullptr;        // device result slot
-  double* h_out = nullptr;        // pinned result slot
+  double* h_out = nullptr;        // mapped pinned result slot (host view)
+  double* h_out_dev = nullptr;    // the same slot as kernels address it
   // xs_sum_host staging ring
   double* stage[2] = {nullptr, nullptr};
   size_t stage_elems = 0;

@@ -169,14 +169,21 @@ def _ptr(x) -> int | None:
     raise TypeError(f"cannot take a pointer of {type(x)}")
 
 
+_torch = None
+
+
 def _stream(s) -> int | None:
+    global _torch
     if s is None:
-        try:
-            import torch
-            if torch.cuda.is_available() and torch.cuda.is_initialized():
-                return torch.cuda.current_stream().cuda_stream
-        except ImportError:
-            pass
+        if _torch is None:
+            try:
+                import torch
+            except ImportError:
+                return None
+            _torch = torch
+        # is_initialized() is a flag test; once CUDA is up, torch's current stream
+        if _torch.cuda.is_initialized():
+            return _torch.cuda.current_stream().cuda_stream
         return None
     if isinstance(s, int):
         return s
