@@ -58,12 +58,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   const long long nfull = sp.npairs / TP;  // tiles without a ragged end
   const long long G = gridDim.x;
   long long t = blockIdx.x;
+  // the first tiles stream into L2 while the accumulator is cleared (and
+  // while a previous grid on the stream may still be finishing)
   if (tid == 0)
-    for (int k = 1; k <= a.prefetch; ++k) prefetch_tile<BLOCK, UNROLL>(sp, t + k * G, ntiles);
-  // the first tile's loads are in flight while the accumulator is cleared
+    for (int k = 0; k <= a.prefetch; ++k) prefetch_tile<BLOCK, UNROLL>(sp, t + k * G, ntiles);
+  for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
+  grid_dependency_wait();
   ulonglong2 A[UNROLL], B[UNROLL];
   if (t < nfull) load_full<BLOCK, UNROLL>(sp, t, tid, A);
-  for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
   if (blockIdx.x == 0 && tid == 0) {
     const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
     if (sp.head) T.one<BLOCK>(xb[0]);
@@ -97,6 +99,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
     T.group_spec<BLOCK, UNROLL>(A);  // the -0 padding is taken back: once per launch
   }
   __syncthreads();
+  grid_launch_dependents();
   unsigned f = T.flags();
   if (blockIdx.x == 0 && tid == 0 && a.n > 0) f |= kFlagAny;
   block_small_to_global<BLOCK>(smem_small, a, f, T.nkey);
@@ -116,6 +119,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_sum_large(SumArgs a) {
   const int tid = threadIdx.x;
   large_init(L, tid, BLOCK);
   __syncthreads();
+  grid_dependency_wait();
 
   const Split sp = split_input(a.x, a.n);
   if (blockIdx.x == 0) {  // unaligned head and odd tail, with the special path
@@ -164,6 +168,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_sum_large(SumArgs a) {
     }
   }
   __syncthreads();
+  grid_launch_dependents();
   large_flush(L, tid, BLOCK);
   __syncthreads();
   if (tid < kSChunks) {
@@ -446,8 +451,20 @@ xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState
   a.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * K.unroll));
   a.prefetch = prefetch_tiles(kSumPrefetch);
   a.divisor = divisor;
-  K.fn<<<(unsigned)g, K.block, K.smem, s>>>(a);
-  XS_TRY_CUDA(cudaGetLastError());
+  // programmatic stream serialization: this grid may be scheduled while the
+  // previous kernel on the stream finishes; the kernel waits for it before
+  // its first load (grid_dependency_wait)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g);
+  cfg.blockDim = dim3((unsigned)K.block);
+  cfg.dynamicSmemBytes = K.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  XS_TRY_CUDA(cudaLaunchKernelEx(&cfg, K.fn, a));
   return XS_OK;
 }
 

@@ -89,6 +89,19 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Programmatic dependent launch (the single-array kernels are launched with
+// programmatic stream serialization): a grid may start while the previous
+// grid on its stream finishes. wait: block until that grid has completed and
+// its writes are visible (a no-op for an ordinary launch); everything before
+// it may only touch shared memory or prefetch into L2 (which is coherent).
+// launch_dependents: this block no longer holds the next grid back.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // --------------------------------------------------------------------------
 // Small superaccumulator, one per thread, chunks strided by `stride` longs.
 // --------------------------------------------------------------------------
