@@ -451,20 +451,7 @@ xs_status launch_sum(DeviceCtx* ctx, const double* d_values, int64_t n, AccState
   a.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * K.unroll));
   a.prefetch = prefetch_tiles(kSumPrefetch);
   a.divisor = divisor;
-  // programmatic stream serialization: this grid may be scheduled while the
-  // previous kernel on the stream finishes; the kernel waits for it before
-  // its first load (grid_dependency_wait)
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)g);
-  cfg.blockDim = dim3((unsigned)K.block);
-  cfg.dynamicSmemBytes = K.smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  XS_TRY_CUDA(cudaLaunchKernelEx(&cfg, K.fn, a));
+  XS_TRY_CUDA(launch_pdl(K.fn, (unsigned)g, (unsigned)K.block, K.smem, s, a));
   return XS_OK;
 }
 

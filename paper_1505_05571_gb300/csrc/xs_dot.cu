@@ -63,11 +63,6 @@ __global__ void __launch_bounds__(BLOCK, 1) k_dot_small(DotArgs d) {
   auto y_at = [&](long long i) -> unsigned long long {
     return (unsigned long long)__double_as_longlong(KIND == 0 ? d.y[i] : a.x[i]);
   };
-  if (blockIdx.x == 0 && tid == 0) {
-    const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
-    if (sp.head) T.one<BLOCK>(canon_nan(product_bits(xb[0], y_at(0))));
-    if (sp.tail) T.one<BLOCK>(canon_nan(product_bits(xb[a.n - 1], y_at(a.n - 1))));
-  }
   constexpr long long TP = (long long)BLOCK * UNROLL;
   const long long ntiles = (sp.npairs + TP - 1) / TP;
   const long long G = gridDim.x;
@@ -142,7 +137,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_dot_small(DotArgs d) {
   };
   long long t = blockIdx.x;
   if (tid == 0)
-    for (int k = 1; k <= a.prefetch; ++k) prefetch(t + k * G);
+    for (int k = 0; k <= a.prefetch; ++k) prefetch(t + k * G);
+  grid_dependency_wait();
+  if (blockIdx.x == 0 && tid == 0) {
+    const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
+    if (sp.head) T.one<BLOCK>(canon_nan(product_bits(xb[0], y_at(0))));
+    if (sp.tail) T.one<BLOCK>(canon_nan(product_bits(xb[a.n - 1], y_at(a.n - 1))));
+  }
   ulonglong2 XA[UNROLL], YA[UNROLL], XB[UNROLL], YB[UNROLL], PA[UNROLL], PB[UNROLL];
   if (t < ntiles) {
     load(t, XA, YA);
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_dot_small(DotArgs d) {
     t += G;
   }
   __syncthreads();
+  grid_launch_dependents();
   unsigned f = T.flags();
   if (blockIdx.x == 0 && tid == 0 && a.n > 0) f |= kFlagAny;
   block_small_to_global<BLOCK>(smem_dot, a, f, T.nkey);
@@ -224,8 +226,7 @@ xs_status launch_dot(const double* x, const double* y, int64_t n, double* d_out,
   d.s.prefetch = prefetch_tiles(kDotPrefetch);
   d.s.divisor = 0ull;
   d.y = kind == 0 ? y : x;
-  fn<<<(unsigned)g, kDotBlock, smem, s>>>(d);
-  XS_TRY_CUDA(cudaGetLastError());
+  XS_TRY_CUDA(launch_pdl(fn, (unsigned)g, (unsigned)kDotBlock, smem, s, d));
   return set_error(XS_OK);
 }
 

@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_sum_f32(F32Args a) {
   const int tail = (int)((a.n - head) - nq * 4);
   const uint4* xq = reinterpret_cast<const uint4*>(a.x + head);
   const unsigned* xb = reinterpret_cast<const unsigned*>(a.x);
+  grid_dependency_wait();
   if (blockIdx.x == 0 && tid == 0) {
     for (int k = 0; k < head; ++k) T.one<BLOCK>(xb[k]);
     for (int k = 0; k < tail; ++k) T.one<BLOCK>(xb[a.n - 1 - k]);
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_sum_f32(F32Args a) {
     t += G;
   }
   __syncthreads();
+  grid_launch_dependents();
   // block partial: slot s of every thread split into its low 32 bits and its
   // high part (owed to the next chunk), summed by warp s % (BLOCK / 32) and
   // added to the grid's signed chunk (s & 7) with the sign of the slot set
@@ -368,7 +370,6 @@ extern "C" xs_status xs_sum_f32_async(const float* d_values, int64_t n, float* d
   a.carry_tiles = std::max(1, (kF32CarryInterval - 7) / (4 * kF32Unroll));
   a.prefetch = prefetch_tiles(kF32Prefetch);
   const long long g = std::max<long long>(1, std::min<long long>((long long)ctx->num_sms * std::max(1, occ), ntiles));
-  k_sum_f32<kF32Block, kF32Unroll><<<(unsigned)g, kF32Block, smem, s>>>(a);
-  XS_TRY_CUDA(cudaGetLastError());
+  XS_TRY_CUDA(launch_pdl(k_sum_f32<kF32Block, kF32Unroll>, (unsigned)g, (unsigned)kF32Block, smem, s, a));
   return set_error(XS_OK);
 }

@@ -84,6 +84,26 @@ constexpr int kSumPrefetch = 3;  // FP64 sum and mean kernels
 constexpr int kDotPrefetch = 3;  // dot and squared-norm kernels
 constexpr int kF32Prefetch = 0;  // binary32 sum kernel (measured: prefetching made it re-read 12 %)
 
+// Launch with programmatic stream serialization: the grid may be scheduled
+// while the previous kernel on the stream finishes. Every kernel launched this
+// way calls grid_dependency_wait() before its first global-memory access
+// (other than L2 prefetches).
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace xs
