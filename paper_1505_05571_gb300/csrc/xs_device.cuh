@@ -626,11 +626,19 @@ __device__ __noinline__ static bool warp_divide(long long& v0, long long& v1, lo
   const int h = b2 ? 64 + 31 - __clz(b2) : (b1 ? 32 + 31 - __clz(b1) : 31 - __clz(b0));
   unsigned long long rem = 0ull;
   if (d <= 0xFFFFFFFFull) {
+    // Only the top four chunks T are divided: with A = T * 2^K + L (L < 2^K)
+    // and T = Q d + R, A / d = Q 2^K + F where 0 <= F < 2^K and F > 0 exactly
+    // when R or L is nonzero; T >= 2^96 and d < 2^32 give Q more than 64
+    // bits, so Q and that sticky bit decide the rounding. (Below four chunks
+    // every chunk is divided and nothing is dropped.)
+    const int kmin = h >= 3 ? h - 3 : 0;
+    const bool low_nonzero =
+        ((b0 & lanes_below(kmin)) | (b1 & lanes_below(kmin - 32)) | (b2 & lanes_below(kmin - 64))) != 0u;
     // cur = rem * 2^32 + chunk < 2^64 (for the top chunk, chunk < 2^34 and
     // rem = 0); q from the integer reciprocal m = floor((2^64 - 1) / d) is at
     // most two below the truth
     const unsigned long long m = 0xFFFFFFFFFFFFFFFFull / d;
-    for (int k = h; k >= 0; --k) {
+    for (int k = h; k >= kmin; --k) {
       const int slot = k >> 5;
       const long long sv = slot == 0 ? v0 : (slot == 1 ? v1 : v2);
       const unsigned long long limb = (unsigned long long)__shfl_sync(kFull, sv, k & 31);
@@ -645,7 +653,10 @@ __device__ __noinline__ static bool warp_divide(long long& v0, long long& v1, lo
         else v2 = (long long)q;
       }
     }
-    return rem != 0ull;
+    if (lane < kmin) v0 = 0;
+    if (lane + 32 < kmin) v1 = 0;
+    if (lane + 64 < kmin) v2 = 0;
+    return rem != 0ull || low_nonzero;
   }
   const double inv = 1.0 / (double)d;
   for (int k = h; k >= 0; --k) {

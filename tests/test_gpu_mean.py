@@ -76,3 +76,35 @@ def test_accumulator_division_by_any_divisor():
         xsum.xs_acc_round_div(h, D, out)
         assert int(bits_of(out)[0]) == xo.finish_div(st, D), D
     xsum.xs_acc_destroy(h)
+
+
+def _doubles_summing_to(S: int) -> list[int]:
+    """Bit patterns of doubles whose exact sum is S * 2^-1074 (S >= 0): greedy
+    53-bit pieces from the top, each exactly representable."""
+    out = []
+    while S:
+        sh = max(0, S.bit_length() - 53)
+        piece = (S >> sh) << sh
+        out.append(f2b(float(__import__("fractions").Fraction(piece, 1 << 1074))))
+        S -= piece
+    return out
+
+
+@pytest.mark.parametrize("d", [3, 5, 7, 64, 1000003])
+@pytest.mark.parametrize("y", [1.0, 0.1, 3.0e300 / 7, 2.0 ** -1000])
+def test_mean_ties_decided_by_the_lowest_chunk(d, y):
+    """Sums with sum / n exactly halfway between two doubles (ties to even),
+    and the same plus the smallest subnormal, which sits in chunk 0 far below
+    the quotient's top: only the sticky part of the division breaks the tie."""
+    Y = int(__import__("fractions").Fraction(y) * (1 << 1074))
+    e = max(1, (Y.bit_length() - 53) + 1)  # ulp of y in units of 2^-1074 (normal y)
+    U = 1 << (e - 1)
+    for r in (0, 1):
+        S = d * (2 * Y + U) // 2 + r if (d * U) % 2 == 0 else None
+        if S is None:
+            continue
+        terms = _doubles_summing_to(S)
+        if len(terms) > d:
+            continue
+        x = np.array(terms + [0] * (d - len(terms)), dtype=np.uint64)
+        assert gpu_mean(x) == c_oracle.mean_bits(x), (d, y, r)
