@@ -215,7 +215,8 @@ xs_status xs_sum_segments(const double* d_values, const int64_t* d_offsets, int6
 typedef struct xs_seg_plan_s* xs_seg_plan;
 /* Tunables of the segmented kernel; zero fields take the tuned or default value. */
 typedef struct xs_seg_options {
-  int block;         /* threads per block of the persistent kernel */
+  int block;         /* threads per work group of a long-segment tile (128, 192, 256 or 384;
+                        groups of 128 and 192 run three or two to one 384-thread block) */
   int unroll;        /* 16-byte loads per thread per tile */
   int tile_elems;    /* elements per block work item of a long segment */
   int short_max;     /* segments up to this length are summed by one warp */

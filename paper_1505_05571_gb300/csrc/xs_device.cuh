@@ -393,12 +393,15 @@ __device__ __forceinline__ unsigned long long warp_max_ull(unsigned long long v)
 // Lane 0 hands the two sums to `emit(chunk, value)`, which adds them into the
 // target accumulator (global or shared). Sums stay below 2^41 in magnitude.
 // Only chunks c_lo..c_hi are read (the others must be zero in every thread).
-template <int BLOCK, typename Emit>
-__device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit, int c_lo = 0,
-                                                 int c_hi = kSChunks - 1) {
-  static_assert(BLOCK % 32 == 0 && BLOCK <= 512, "digit sums sized for up to 16 warps");
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = BLOCK / 32;
+// The group form sums the NT consecutive threads whose chunk 0 starts at sm
+// (accumulators strided by STRIDE); gwarp is the warp's index in the group.
+template <int STRIDE, int NT, typename Emit>
+__device__ __forceinline__ void group_chunk_sums(const long long* sm, int gwarp, Emit emit,
+                                                 int c_lo = 0, int c_hi = kSChunks - 1) {
+  static_assert(NT % 32 == 0 && NT <= 512, "digit sums sized for up to 16 warps");
+  const int lane = threadIdx.x & 31, warp = gwarp;
+  constexpr int NW = NT / 32;
+  constexpr int BLOCK = STRIDE;
   constexpr int BATCH = 6;
   for (int c0 = c_lo + warp; c0 <= c_hi; c0 += BATCH * NW) {
     unsigned long long lo[BATCH];
@@ -437,6 +440,12 @@ __device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit,
       }
     }
   }
+}
+
+template <int BLOCK, typename Emit>
+__device__ __forceinline__ void block_chunk_sums(const long long* sm, Emit emit, int c_lo = 0,
+                                                 int c_hi = kSChunks - 1) {
+  group_chunk_sums<BLOCK, BLOCK>(sm, (int)(threadIdx.x >> 5), emit, c_lo, c_hi);
 }
 
 // --------------------------------------------------------------------------

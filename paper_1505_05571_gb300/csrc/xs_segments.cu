@@ -182,17 +182,42 @@ __device__ __forceinline__ void prefetch_range(const unsigned long long* p,
   }
 }
 
-template <int BLOCK, int UNROLL>
-__global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
-  static_assert(BLOCK >= 64, "warp 1 claims and prefetches the next tile");
+// Launch shape of the segmented kernel for phase-1 work groups of W threads:
+// a block of 384 threads (one per SM, 12 warps) holding 384 / W groups when W
+// divides 384 -- measured on GB300, several blocks per SM accumulate about
+// 10 % slower than one block of the same total size -- else one group per block.
+template <int W>
+struct SegShape {
+  static constexpr int block = (384 % W == 0) ? 384 : W;
+  static constexpr int groups = block / W;
+};
+
+template <int W, int UNROLL>
+__global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
+  constexpr int BLOCK = SegShape<W>::block;
+  constexpr int NG = SegShape<W>::groups;
+  static_assert(W >= 96 && W % 32 == 0, "warp 1 of a group claims the next tile; 67 chunk sums");
   extern __shared__ __align__(16) long long smem_seg[];
-  __shared__ long long bsum[kSChunks];
-  __shared__ long long s_item;
-  __shared__ unsigned s_flags;
-  __shared__ unsigned long long s_nkey;
-  __shared__ unsigned s_last;
-  __shared__ unsigned s_emin, s_emax;
+  __shared__ long long g_bsum[NG][kSChunks];
+  __shared__ long long g_item[NG];
+  __shared__ long long g_meta[NG][4];
+  __shared__ unsigned g_flags[NG], g_last[NG], g_emin[NG], g_emax[NG];
+  __shared__ unsigned long long g_nkey[NG];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = tid / W, gt = tid - grp * W, gwarp = gt >> 5;  // group, rank and warp in it
+  long long* bsum = g_bsum[grp];
+  long long& s_item = g_item[grp];
+  long long* s_meta = g_meta[grp];
+  unsigned& s_flags = g_flags[grp];
+  unsigned& s_last = g_last[grp];
+  unsigned& s_emin = g_emin[grp];
+  unsigned& s_emax = g_emax[grp];
+  unsigned long long& s_nkey = g_nkey[grp];
+  // barrier of the group's W threads (named barrier 1 + group)
+  auto gsync = [&]() {
+    if (NG == 1) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(W) : "memory");
+  };
   SmallThread T;
   T.acc = smem_seg + tid;
   // The accumulators are cleared once; every merge clears again the chunks it
@@ -202,11 +227,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
   const long long ntiles = (long long)a.counters[0];
   const long long nshort = (long long)a.counters[1];
   const unsigned long long* xb_all = reinterpret_cast<const unsigned long long*>(a.x);
+  __syncthreads();
 
-  // ---- phase 1: tiles of long segments, one block each ----
-  // The next tile is claimed while the block merges the current one, and its
-  // start is prefetched into L2 before the block moves on, so neither the
-  // claim nor a tile's first loads wait behind the previous merge.
+  // ---- phase 1: tiles of long segments, one work group of W threads each ----
+  // Each group claims tiles on its own. The next tile is claimed while the
+  // group merges the current one, and its start is prefetched into L2 before
+  // the group moves on, so neither the claim nor a tile's first loads wait
+  // behind the previous merge.
   // segment of tile t: from the table, else the last s with tile_start[s] <= t
   auto segment_of = [&](long long t) -> long long {
     if (ntiles <= a.tile_cap) return a.tile_seg[t];
@@ -218,7 +245,6 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     return lo_s;
   };
   // where tile t lies: its segment, element range and the segment's tile count
-  __shared__ long long s_meta[4];
   auto describe = [&](long long t) {
     const long long sg = segment_of(t);
     const long long ft = a.tile_start[sg];
@@ -228,24 +254,24 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     s_meta[2] = min(tl + a.tile_elems, a.off[sg + 1]);
     s_meta[3] = a.tile_start[sg + 1] - ft;
   };
-  if (tid == 0) {
+  if (gt == 0) {
     s_item = (long long)atomicAdd(&a.counters[2], 1ull);
     if (s_item < ntiles) describe(s_item);
   }
   for (;;) {
-    if (tid < kSChunks) bsum[tid] = 0;
-    if (tid == 0) {
+    for (int c = gt; c < kSChunks; c += W) bsum[c] = 0;
+    if (gt == 0) {
       s_flags = 0u;
       s_nkey = 0ull;
       s_emin = 0x7FFu;
       s_emax = 0u;
     }
-    __syncthreads();
+    gsync();
     const long long t = s_item;
     if (t >= ntiles) break;
     const long long s = s_meta[0], lo = s_meta[1], hi = s_meta[2], seg_tiles = s_meta[3];
     T.reset();
-    accumulate_range<BLOCK, UNROLL, true, true>(T, a.x, lo, hi, tid, BLOCK);
+    accumulate_range<BLOCK, UNROLL, true, true>(T, a.x, lo, hi, gt, W);
     {
       const unsigned wmin = __reduce_min_sync(kFull, T.emin);
       const unsigned wmax = __reduce_max_sync(kFull, T.emax);
@@ -254,8 +280,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
         atomicMax(&s_emax, wmax);
       }
     }
-    __syncthreads();  // every thread has read s_item; the window is complete
-    if (tid == 32) s_item = (long long)atomicAdd(&a.counters[2], 1ull);
+    gsync();  // every thread has read s_item; the window is complete
+    if (gt == 32) s_item = (long long)atomicAdd(&a.counters[2], 1ull);
     const int cmin = (int)(s_emin >> kLowExpBits);
     const int cmax = s_emax >= s_emin ? (int)(s_emax >> kLowExpBits) + 1 : cmin - 1;  // empty
     unsigned f = __reduce_or_sync(kFull, T.flags());
@@ -264,13 +290,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
       if (f) atomicOr(&s_flags, f);
       if (k) atomicMax(&s_nkey, k);
     }
+    const long long* gacc = smem_seg + grp * W;  // the group's accumulators
     if (seg_tiles == 1) {
-      block_chunk_sums<BLOCK>(smem_seg, [&](int c, long long v) {
+      group_chunk_sums<BLOCK, W>(gacc, gwarp, [&](int c, long long v) {
         atomicAdd(reinterpret_cast<unsigned long long*>(bsum + c), (unsigned long long)v);
       }, cmin, cmax);
-      __syncthreads();
+      gsync();
       for (int c = cmin; c <= cmax; ++c) T.acc[c * BLOCK] = 0;
-      if (warp == 0) {
+      if (gwarp == 0) {
         const long long v0 = bsum[lane], v1 = bsum[lane + 32], v2 = lane < 3 ? bsum[lane + 64] : 0;
         __syncwarp();  // bsum is the rounding scratch from here on
         const unsigned long long r = warp_round(v0, v1, v2, s_flags | kFlagAny, s_nkey, bsum, 32);
@@ -279,19 +306,19 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
     } else {
       AccState* g = a.slots + a.slot_of[s];
       unsigned long long* gc = reinterpret_cast<unsigned long long*>(g->chunk);
-      block_chunk_sums<BLOCK>(smem_seg, [&](int c, long long v) {
+      group_chunk_sums<BLOCK, W>(gacc, gwarp, [&](int c, long long v) {
         if (v != 0) atomicAdd(gc + c, (unsigned long long)v);
       }, cmin, cmax);
-      __syncthreads();
+      gsync();
       for (int c = cmin; c <= cmax; ++c) T.acc[c * BLOCK] = 0;
-      if (tid == 0) {
+      if (gt == 0) {
         if (s_flags) atomicOr(&g->flags, s_flags);
         if (s_nkey) atomicMax(&g->nan_key, s_nkey);
         __threadfence();
         s_last = (atomicAdd(&g->ticket, 1u) == (unsigned)(seg_tiles - 1)) ? 1u : 0u;
       }
-      __syncthreads();
-      if (s_last && warp == 0) {
+      gsync();
+      if (s_last && gwarp == 0) {
         __threadfence();
         const long long v0 = (long long)atomicExch(gc + lane, 0ull);
         const long long v1 = (long long)atomicExch(gc + lane + 32, 0ull);
@@ -309,15 +336,15 @@ __global__ void __launch_bounds__(BLOCK, 1) k_seg_main(SegArgs a) {
         if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
       }
     }
-    if (tid == 32) {  // the next tile: where it lies, and its first groups into L2
+    if (gt == 32) {  // the next tile: where it lies, and its first groups into L2
       const long long tn = s_item;  // beside warp 0's rounding
       if (tn < ntiles) {
         describe(tn);
         prefetch_range(xb_all + s_meta[1],
-                       xb_all + min(s_meta[2], s_meta[1] + (long long)kPhase1Ahead * BLOCK));
+                       xb_all + min(s_meta[2], s_meta[1] + (long long)kPhase1Ahead * W));
       }
     }
-    __syncthreads();
+    gsync();
   }
 
   // ---- phase 2: short segments, one warp each ----
@@ -447,13 +474,16 @@ typedef void (*SegKernel)(SegArgs);
 struct SegEntry {
   int block, unroll;
   SegKernel fn;
+  int launch;  // threads per launched block
 };
+// block: the phase-1 work group (threads of the launch: SegShape<block>::block)
 const SegEntry kSeg[] = {
-    {128, 4, k_seg_main<128, 4>},
-    {192, 4, k_seg_main<192, 4>},
-    {256, 4, k_seg_main<256, 4>},
-    {384, 4, k_seg_main<384, 4>},
-    {192, 8, k_seg_main<192, 8>},
+    {128, 4, k_seg_main<128, 4>, SegShape<128>::block},
+    {192, 4, k_seg_main<192, 4>, SegShape<192>::block},
+    {256, 4, k_seg_main<256, 4>, SegShape<256>::block},
+    {384, 4, k_seg_main<384, 4>, SegShape<384>::block},
+    {192, 8, k_seg_main<192, 8>, SegShape<192>::block},
+    {128, 8, k_seg_main<128, 8>, SegShape<128>::block},
 };
 constexpr int kNumSeg = sizeof(kSeg) / sizeof(kSeg[0]);
 
@@ -520,7 +550,7 @@ static xs_status plan_enqueue(xs_seg_plan p, cudaStream_t s) {
   k_seg_fill<<<nb, kPrepThreads, 0, s>>>(p->args);
   XS_TRY_CUDA(cudaGetLastError());
   const SegEntry& K = kSeg[p->kernel];
-  K.fn<<<p->grid, K.block, seg_smem(K.block), s>>>(p->args);
+  K.fn<<<p->grid, K.launch, seg_smem(K.launch), s>>>(p->args);
   XS_TRY_CUDA(cudaGetLastError());
   return XS_OK;
 }
@@ -548,13 +578,13 @@ xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const in
     static bool attr_done[64][kNumSeg] = {};
     if (ctx->device < 64 && !attr_done[ctx->device][k]) {
       XS_TRY_CUDA(cudaFuncSetAttribute(kSeg[k].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)seg_smem(o.block)));
+                                       (int)seg_smem(kSeg[k].launch)));
       attr_done[ctx->device][k] = true;
     }
   }
   int occ = 0;
-  XS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kSeg[k].fn, o.block,
-                                                            seg_smem(o.block)));
+  XS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kSeg[k].fn, kSeg[k].launch,
+                                                            seg_smem(kSeg[k].launch)));
   if (occ < 1) return set_error(XS_ERR_NOT_SUPPORTED);
   xs_seg_plan p = new xs_seg_plan_s();
   p->device = ctx->device;
@@ -701,7 +731,7 @@ xs_status xs_autotune_segments(const double* d_values, const int64_t* d_offsets,
   if (!ctx) return st;
   cudaStream_t s = as_stream(stream);
   std::vector<xs_seg_options> cands;
-  const int blocks[][2] = {{128, 4}, {192, 4}, {256, 4}, {384, 4}, {192, 8}};
+  const int blocks[][2] = {{128, 4}, {192, 4}, {256, 4}, {384, 4}, {192, 8}, {128, 8}};
   const int tiles[] = {1 << 16, 1 << 17, 1 << 18};
   const int shorts[] = {1024, 4096, 16384};
   for (auto& b : blocks)

@@ -19,6 +19,7 @@ OPTS = [
     {"block": 256, "unroll": 4, "tile_elems": 1 << 13, "short_max": 4096},
     {"block": 384, "unroll": 4, "tile_elems": 1 << 18, "short_max": 16384},
     {"block": 192, "unroll": 8, "tile_elems": 3000, "short_max": 0},
+    {"block": 128, "unroll": 8, "tile_elems": 1 << 14, "short_max": 256},
 ]
 
 
