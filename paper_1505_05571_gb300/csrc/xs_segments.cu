@@ -498,12 +498,13 @@ size_t seg_smem(int block) { return (size_t)block * kSChunks * sizeof(long long)
 xs_seg_options default_seg_options(DeviceCtx* ctx) {
   if (ctx->have_tuned_seg) return ctx->tuned_seg;
   xs_seg_options o;
-  // measured on GB300 over the config-3 length law: 192 x 8 (5,000 and
-  // 100,000 segments 4-6 % faster than 192 x 4; uniform 10^4..10^5-value
-  // segments favour 128 x 4 -- xs_autotune_segments picks per workload)
-  o.block = 192;
+  // measured on GB300 over the config-3 length law (100,000 segments):
+  // groups of 128 x 8 with tiles of 2^17 values 11.33 ms, 192 x 8 11.53 ms,
+  // 192 x 4 12.25 ms; uniform 10^4-value segments favour 128 x 4 --
+  // xs_autotune_segments picks per workload
+  o.block = 128;
   o.unroll = 8;
-  o.tile_elems = 1 << 18;
+  o.tile_elems = 1 << 17;
   o.short_max = 4096;
   o.carry_tiles = 0;
   return o;
