@@ -62,39 +62,76 @@ struct BatchArgs {
 constexpr int kServeBlock = 192;
 constexpr int kServeUnroll = 4;
 
+// L2 prefetch of the 16-byte-aligned part of [p, q), in pieces of at most 64 KB.
+__device__ __forceinline__ void serve_prefetch(const double* p, const double* q) {
+  uintptr_t b0 = ((uintptr_t)p + 15u) & ~(uintptr_t)15u;
+  const uintptr_t b1 = (uintptr_t)q & ~(uintptr_t)15u;
+  while (b0 < b1) {
+    const uintptr_t n = min(b1 - b0, (uintptr_t)65536u);
+    prefetch_l2((const void*)b0, (unsigned)n);
+    b0 += n;
+  }
+}
+
 template <int BLOCK, int UNROLL>
 __global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
+  static_assert(BLOCK >= 96, "warp 1 claims the next tile; 67 chunk sums");
   extern __shared__ __align__(16) long long smem_srv[];
+  __shared__ long long sc[kSChunks];  // rounding scratch
   __shared__ long long s_tile;
-  __shared__ unsigned s_flags;
+  __shared__ int s_item;
+  __shared__ unsigned s_flags, s_last, s_emin, s_emax;
   __shared__ unsigned long long s_nkey;
-  __shared__ unsigned s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   SmallThread T;
   T.acc = smem_srv + tid;
+  // Accumulators are cleared once and every merge clears the window of
+  // chunks it read, so they are zero whenever a tile starts.
+  for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
   const long long total = a.hdr->total_tiles;
   const int nitems = a.hdr->nitems;
-  for (;;) {
-    if (tid == 0) {
-      s_tile = (long long)atomicAdd(&a.hdr->cursor, 1ull);
-      s_flags = 0u;
-      s_nkey = 0ull;
-    }
-    __syncthreads();
-    const long long t = s_tile;
-    if (t >= total) break;
-    int lo_i = 0, hi_i = nitems;  // last item with tile0 <= t
+  // the last item with tile0 <= t
+  auto item_of = [&](long long t) -> int {
+    int lo_i = 0, hi_i = nitems;
     while (hi_i - lo_i > 1) {
       const int mid = (lo_i + hi_i) >> 1;
       if (a.items[mid].tile0 <= t) lo_i = mid; else hi_i = mid;
     }
-    const BatchItem it = a.items[lo_i];
+    return lo_i;
+  };
+  // The next tile is claimed and located while the block merges the current
+  // one, and its start is prefetched into L2.
+  if (tid == 0) {
+    s_tile = (long long)atomicAdd(&a.hdr->cursor, 1ull);
+    if (s_tile < total) s_item = item_of(s_tile);
+  }
+  for (;;) {
+    if (tid == 0) {
+      s_flags = 0u;
+      s_nkey = 0ull;
+      s_emin = 0x7FFu;
+      s_emax = 0u;
+    }
+    __syncthreads();
+    const long long t = s_tile;
+    if (t >= total) break;
+    const BatchItem it = a.items[s_item];
     const long long first = (t - it.tile0) * a.tile_elems;
     const long long end = min(first + a.tile_elems, it.n);
-    for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
     T.reset();
-    if (first < end) accumulate_range<BLOCK, UNROLL, true>(T, it.x, first, end, tid, BLOCK);
-    __syncthreads();
+    if (first < end) accumulate_range<BLOCK, UNROLL, true, true>(T, it.x, first, end, tid, BLOCK);
+    {
+      const unsigned wmin = __reduce_min_sync(kFull, T.emin);
+      const unsigned wmax = __reduce_max_sync(kFull, T.emax);
+      if (lane == 0 && wmax >= wmin) {
+        atomicMin(&s_emin, wmin);
+        atomicMax(&s_emax, wmax);
+      }
+    }
+    __syncthreads();  // every thread has read s_tile and s_item; the window is complete
+    if (tid == 32) s_tile = (long long)atomicAdd(&a.hdr->cursor, 1ull);
+    const int cmin = (int)(s_emin >> kLowExpBits);
+    const int cmax = s_emax >= s_emin ? (int)(s_emax >> kLowExpBits) + 1 : cmin - 1;  // empty
     unsigned f = __reduce_or_sync(kFull, T.flags());
     const unsigned long long k = warp_max_ull(T.nkey);
     if (lane == 0) {
@@ -105,8 +142,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
     unsigned long long* gc = reinterpret_cast<unsigned long long*>(g->chunk);
     block_chunk_sums<BLOCK>(smem_srv, [&](int c, long long v) {
       if (v != 0) atomicAdd(gc + c, (unsigned long long)v);
-    });
+    }, cmin, cmax);
     __syncthreads();
+    for (int c = cmin; c <= cmax; ++c) T.acc[c * BLOCK] = 0;
     if (tid == 0) {
       unsigned fl = s_flags | ((it.n > 0 && t == it.tile0) ? kFlagAny : 0u);
       if (fl) atomicOr(&g->flags, fl);
@@ -130,17 +168,28 @@ __global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
         }
         fl = __shfl_sync(kFull, fl, 0);
         key = __shfl_sync(kFull, key, 0);
-        const unsigned long long r = warp_round(v0, v1, v2, fl, key, smem_srv, 32);
+        const unsigned long long r = warp_round(v0, v1, v2, fl, key, sc, 32);
         if (lane == 0 && it.res_idx >= 0) a.results[it.res_idx] = r;
       } else {  // keep the exact sum, in canonical form
         long long v0 = (long long)__ldcg(gc + lane);
         long long v1 = (long long)__ldcg(gc + lane + 32);
         long long v2 = lane < 3 ? (long long)__ldcg(gc + lane + 64) : 0;
-        warp_normalize(v0, v1, v2, smem_srv, 32);
+        warp_normalize(v0, v1, v2, sc, 32);
         gc[lane] = (unsigned long long)v0;
         gc[lane + 32] = (unsigned long long)v1;
         if (lane < 3) gc[lane + 64] = (unsigned long long)v2;
         if (lane == 0) g->ticket = 0u;
+      }
+    }
+    if (tid == 32) {  // where the next tile lies, and its start into L2 (beside warp 0)
+      const long long tn = s_tile;
+      if (tn < total) {
+        const int in = item_of(tn);
+        s_item = in;
+        const BatchItem& nx = a.items[in];
+        const long long nf = (tn - nx.tile0) * a.tile_elems;
+        const long long ne = min(min(nf + a.tile_elems, nx.n), nf + 48LL * BLOCK);
+        if (nf < ne) serve_prefetch(nx.x + nf, nx.x + ne);
       }
     }
     __syncthreads();
