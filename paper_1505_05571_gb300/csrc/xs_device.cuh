@@ -169,6 +169,10 @@ __device__ __noinline__ static void take_back(long long* __restrict__ a, unsigne
 // ([emin, emax], empty while emax < emin) is kept as well, so a merge can
 // read, and clear, only the chunks those terms touched (Discussion: low
 // fixed cost when few chunks are in use).
+// A positional exponent past 2046 whose window, (e >> 5) + 1, is the top chunk:
+// set as emax once a carry propagation may have filled the chunks above.
+constexpr unsigned kWindowTop = (kSChunks - 2) << kLowExpBits;
+
 struct SmallThread {
   long long* acc;  // this thread's chunks, stride BLOCK
   unsigned notnegz = 0u;  // saw a term other than -0
@@ -316,7 +320,8 @@ __device__ __forceinline__ void sacc_propagate(long long* __restrict__ a, int st
 // the range into L2 a few groups ahead.
 template <int BLOCK, int UNROLL, bool PREFETCH, bool TRACK = false>
 __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x, long long lo,
-                                                 long long hi, int r, int nthr) {
+                                                 long long hi, int r, int nthr,
+                                                 int carry_groups = 0) {
   const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(x);
   long long p = lo;
   if (p < hi && (((uintptr_t)(x + p)) & 15u) != 0u) {
@@ -345,6 +350,17 @@ __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x
   };
   if (PREFETCH)
     for (int k = 1; k <= kAhead; ++k) prefetch(k);
+  // carry_groups > 0: propagate carries after that many groups (ranges longer
+  // than 2047 adds per thread); afterwards chunks up to the top may be nonzero,
+  // which the window records as kWindowTop
+  int since = 0;
+  auto tick = [&]() {
+    if (carry_groups > 0 && ++since >= carry_groups) {
+      sacc_propagate(T.acc, BLOCK);
+      if (TRACK) T.emax = kWindowTop;
+      since = 0;
+    }
+  };
   ulonglong2 A[UNROLL], B[UNROLL];
   long long g = 0;
   if (nfull > 0) load_full(0, A);
@@ -352,10 +368,12 @@ __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x
     prefetch(g + kAhead + 1);
     if (g + 1 < nfull) load_full(g + 1, B);
     T.group_spec<BLOCK, UNROLL, TRACK>(A);
+    tick();
     if (++g >= nfull) break;
     prefetch(g + kAhead + 1);
     if (g + 1 < nfull) load_full(g + 1, A);
     T.group_spec<BLOCK, UNROLL, TRACK>(B);
+    tick();
     ++g;
   }
   if (nfull * gsz < npairs) {

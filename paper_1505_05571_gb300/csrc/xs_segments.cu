@@ -196,6 +196,9 @@ template <int W, int UNROLL>
 __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
   constexpr int BLOCK = SegShape<W>::block;
   constexpr int NG = SegShape<W>::groups;
+  // groups of adds between carry propagations in a tile: with the head, tail
+  // and padded last group, at most 2045 adds per thread
+  constexpr int kCarryGroups = (kCarryInterval - 4 - 2 * UNROLL) / (2 * UNROLL);
   static_assert(W >= 96 && W % 32 == 0, "warp 1 of a group claims the next tile; 67 chunk sums");
   extern __shared__ __align__(16) long long smem_seg[];
   __shared__ long long g_bsum[NG][kSChunks];
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
     if (t >= ntiles) break;
     const long long s = s_meta[0], lo = s_meta[1], hi = s_meta[2], seg_tiles = s_meta[3];
     T.reset();
-    accumulate_range<BLOCK, UNROLL, true, true>(T, a.x, lo, hi, gt, W);
+    accumulate_range<BLOCK, UNROLL, true, true>(T, a.x, lo, hi, gt, W, kCarryGroups);
     {
       const unsigned wmin = __reduce_min_sync(kFull, T.emin);
       const unsigned wmax = __reduce_max_sync(kFull, T.emax);
@@ -518,8 +521,8 @@ xs_status resolve_options(DeviceCtx* ctx, const xs_seg_options* in, xs_seg_optio
   if (o.tile_elems == 0) o.tile_elems = d.tile_elems;
   if (o.short_max == 0) o.short_max = d.short_max;
   if (find_seg(o.block, o.unroll) < 0) return set_error(XS_ERR_NOT_SUPPORTED);
-  // per-thread adds between carry propagations stay within 2047
-  if (o.tile_elems < 2 * o.block || o.tile_elems > 2040LL * o.block) return set_error(XS_ERR_INVALID_VALUE);
+  // tiles longer than 2040 values per thread propagate carries inside the tile
+  if (o.tile_elems < 2 * o.block || o.tile_elems > (1 << 26)) return set_error(XS_ERR_INVALID_VALUE);
   if (o.short_max < 0 || o.short_max > 2040 * 32) return set_error(XS_ERR_INVALID_VALUE);
   *out = o;
   return XS_OK;

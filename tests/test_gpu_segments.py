@@ -140,3 +140,26 @@ def test_full_cfg3_sampled():
     for s in sample:
         seg = W.cfg3_values(0, int(off[s]), int(lengths[s]))
         assert got[s] == c_oracle.sum_bits(seg), int(s)
+
+
+@pytest.mark.parametrize("tile", [1 << 20, 1 << 22, 3_000_001])
+def test_tiles_longer_than_the_carry_interval(tile):
+    """Tiles of up to 4 Mi values per 128-thread group (about 32,000 adds per
+    thread): carries propagate inside the tile, and the merge window then runs
+    to the top chunk. Same-sign terms at the top of a chunk (the largest
+    adds), a negative segment (carries ripple as 2^32 - 1 chunks), zeros."""
+    rng = np.random.default_rng(tile)
+    lengths = np.array([3_000_017, 5, 4_200_000, 1, 2_500_001], dtype=np.int64)
+    off = W.cfg3_offsets(lengths)
+    n = int(off[-1])
+    e = np.uint64(0x7DF)  # exponent 2015: chunk 62, shift 31
+    vals = (e << np.uint64(52)) | rng.integers(0, 1 << 52, n, dtype=np.uint64)
+    vals[off[2]:off[3]] |= np.uint64(1 << 63)  # the third segment negative
+    vals[rng.integers(0, n, 5000)] = 0
+    expect = c_oracle.segment_sums_bits(vals, off)
+    vd = to_device(vals)
+    od = torch.from_numpy(off).cuda()
+    for opts in ({"block": 128, "unroll": 8, "tile_elems": tile, "short_max": 64},
+                 {"block": 192, "unroll": 4, "tile_elems": tile, "short_max": 0}):
+        got = run_plan(vd, od, lengths.size, opts)
+        assert np.array_equal(got, expect), (opts, [hex(int(g)) for g in got], [hex(int(x)) for x in expect])
