@@ -426,9 +426,12 @@ Workspace* workspace(DeviceCtx* ctx, cudaStream_t s, xs_status* st) {
 SumShape default_shape(DeviceCtx* ctx, int64_t n) {
   auto it = ctx->tuned_sum.find(size_class(n));
   if (it != ctx->tuned_sum.end()) return it->second;
-  // measured on GB300: per-thread small superaccumulators win at every size;
-  // 384 x 6 takes 126.4 us on 1e8 values where 384 x 4 takes 130.0 and 384 x 8 137.6
-  if (n < (int64_t(1) << 20)) return SumShape{XS_METHOD_SMALL, 128, 4};
+  // measured on GB300 (back-to-back launches): per-thread small superaccumulators
+  // win at every size; 256 x 4 is fastest below about 1e5 values (6.3-6.8 us),
+  // 384 x 4 up to about 1e7 (19.6 us at 1e7, where 384 x 6 takes 20.1), and
+  // 384 x 6 beyond (126.4 us on 1e8 values, 384 x 4 130.0, 384 x 8 137.6)
+  if (n < (int64_t(1) << 17)) return SumShape{XS_METHOD_SMALL, 256, 4};
+  if (n < (int64_t(1) << 25)) return SumShape{XS_METHOD_SMALL, 384, 4};
   return SumShape{XS_METHOD_SMALL, 384, 6};
 }
 
