@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
       // Low fixed cost for short sums (Discussion: track the chunks in use
       // instead of clearing and scanning all 67): the terms sit in registers,
       // the warp finds the range of chunk indices they touch, and only that
-      // window is cleared, added into and read back.
+      // window is added into, read back and cleared again.
       unsigned long long v[4];
       int mn = kSChunks, mx = -1;
 #pragma unroll
@@ -424,41 +424,37 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
       cmin = (int)(wmin >> kLowExpBits);
       cmax = wmax >= wmin ? (int)(wmax >> kLowExpBits) + 1 : cmin - 1;  // empty
     }
-    __syncwarp();
-    // lane L gathers chunks L, L+32, L+64 of the warp's 32 accumulators (only
-    // those in the window), split into low and high halves; reads are rotated
-    // by lane to avoid conflicts
-    const long long* wbase = smem_seg + warp * 32;
-    long long lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0, lo2 = 0, hi2 = 0;
-    const bool in0w = lane >= cmin && lane <= cmax;
-    const bool in1w = lane + 32 >= cmin && lane + 32 <= cmax;
-    const bool in2w = lane < 3 && lane + 64 >= cmin && lane + 64 <= cmax;
-    if (in0w | in1w | in2w) {
-      for (int q = 0; q < 32; ++q) {
-        const int src = (q + lane) & 31;
-        const long long u0 = in0w ? wbase[lane * BLOCK + src] : 0;
-        const long long u1 = in1w ? wbase[(lane + 32) * BLOCK + src] : 0;
-        const long long u2 = in2w ? wbase[(lane + 64) * BLOCK + src] : 0;
-        lo0 += u0 & 0xFFFFFFFFll; hi0 += u0 >> 32;
-        lo1 += u1 & 0xFFFFFFFFll; hi1 += u1 >> 32;
-        lo2 += u2 & 0xFFFFFFFFll; hi2 += u2 >> 32;
+    // Warp sums of the window's chunks, one chunk at a time: each lane splits
+    // its own chunk c into the low 32 bits and the signed high part (owed to
+    // chunk c + 1) and clears it; the 32-lane sums come from 32-bit warp
+    // reductions of 16-bit digits (digit sums below 2^21 in magnitude: exact).
+    // Lane L collects chunks L, L + 32 and L + 64 of the sum.
+    long long v0 = 0, v1 = 0, v2 = 0;
+    auto put = [&](int k, long long val) {
+      if (k < 32) { if (lane == k) v0 += val; }
+      else if (k < 64) { if (lane == k - 32) v1 += val; }
+      else if (lane == k - 64) v2 += val;
+    };
+    for (int c = cmin; c <= cmax; ++c) {
+      const long long u = T.acc[c * BLOCK];
+      T.acc[c * BLOCK] = 0;
+      const unsigned lw = (unsigned)u;
+      const int hw = (int)(u >> 32);
+      const unsigned l0 = __reduce_add_sync(kFull, lw & 0xFFFFu);
+      const unsigned l1 = __reduce_add_sync(kFull, lw >> 16);
+      const unsigned h0 = __reduce_add_sync(kFull, (unsigned)hw & 0xFFFFu);
+      const int h1 = __reduce_add_sync(kFull, hw >> 16);
+      const long long sum_lo = (long long)l0 + (long long)l1 * 65536ll;
+      const long long sum_hi = (long long)h0 + (long long)h1 * 65536ll;
+      if (c == kSChunks - 1) {
+        put(c, sum_lo + sum_hi * 4294967296ll);
+      } else {
+        put(c, sum_lo);
+        put(c + 1, sum_hi);
       }
     }
-    // high half of chunk c belongs to chunk c+1 (chunk 66 keeps its own)
-    const long long top_hi = (lane == 2) ? hi2 : 0;
-    long long in0 = __shfl_up_sync(kFull, hi0, 1);
-    long long in1 = __shfl_up_sync(kFull, hi1, 1);
-    long long in2 = __shfl_up_sync(kFull, hi2, 1);
-    const long long w0 = __shfl_sync(kFull, hi0, 31);
-    const long long w1 = __shfl_sync(kFull, hi1, 31);
-    if (lane == 0) { in0 = 0; in1 = w0; in2 = w1; }
-    const long long v0 = lo0 + in0;
-    const long long v1 = lo1 + in1;
-    const long long v2 = lane < 3 ? lo2 + in2 + top_hi * 4294967296ll : 0;
     const unsigned f = __reduce_or_sync(kFull, T.flags()) | kFlagAny;
     const unsigned long long key = warp_max_ull(T.nkey);
-    __syncwarp();  // every lane's gather is done
-    for (int c = cmin; c <= cmax; ++c) T.acc[c * BLOCK] = 0;
     __syncwarp();  // chunks 0..2 of the warp's threads are the rounding scratch now
     const unsigned long long r = warp_round(v0, v1, v2, f, key, smem_seg + warp * 32, BLOCK);
     if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
