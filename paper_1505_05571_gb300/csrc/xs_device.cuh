@@ -625,6 +625,97 @@ __device__ __forceinline__ unsigned long long signed_zero(unsigned flags) {
   return ((flags & kFlagAny) && !(flags & kFlagNotNegZero)) ? kNegZero : 0ull;
 }
 
+// Correctly rounded exact sum of a value known on a window of chunks only:
+// chunk c0 + k holds w[k] (any signed 64-bit value of magnitude below 2^62),
+// k < nw <= NW, every other chunk is zero; the same rounding as warp_round,
+// done by one thread (every lane may call it; no shared memory).
+//   1. Carry propagation gives 32-bit digits d[0..nw) and a signed top carry.
+//   2. A negative value is negated as a digit string (two's complement).
+//   3. The top three digits T (96 bits) and an OR of the digits below give the
+//      53-bit significand, the round bit and the sticky bit of the magnitude A
+//      (in units of 2^-1075; its bit 0 is always zero for sums of doubles, so
+//      A / 2 is the value in units of 2^-1074), then ties to even, a carry into
+//      the next binade and overflow to Inf as in the small section.
+template <int NW>
+__device__ __forceinline__ unsigned long long round_window(const long long (&w)[NW], int nw, int c0,
+                                                           unsigned flags,
+                                                           unsigned long long nan_key) {
+  unsigned long long sp;
+  if (special_result(flags, nan_key, &sp)) return sp;
+  unsigned d[NW + 1];
+  long long carry = 0;
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    const long long x = (k < nw ? w[k] : 0) + carry;
+    d[k] = (unsigned)x;
+    carry = x >> 32;  // arithmetic: floor division by 2^32
+  }
+  const bool neg = carry < 0;
+  if (neg) {  // -(D + carry 2^(32 NW)) = ~D + 1 + (-carry - 1) 2^(32 NW)
+    unsigned long long c = 1;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const unsigned long long x = (unsigned long long)(unsigned)~d[k] + c;
+      d[k] = (unsigned)x;
+      c = x >> 32;
+    }
+    carry = -carry - 1 + (long long)c;
+  }
+  d[NW] = (unsigned)carry;  // 0 <= carry < 2^32 for sums of finite doubles
+  int m = -1;  // the top nonzero digit
+#pragma unroll
+  for (int k = 0; k <= NW; ++k)
+    if (d[k] != 0u) m = k;
+  if (m < 0) return signed_zero(flags);
+  const unsigned long long sign = neg ? kNegZero : 0ull;
+  const unsigned t2 = d[m];
+  unsigned t1 = 0u, t0 = 0u;
+  bool low = false;
+#pragma unroll
+  for (int k = 0; k <= NW; ++k) {
+    if (k == m - 1) t1 = d[k];
+    if (k == m - 2) t0 = d[k];
+    if (k < m - 2 && d[k] != 0u) low = true;
+  }
+  // A = T 2^(32 (c0 + m - 2)) + (lower digits), T = t2:t1:t0
+  const int top = 95 - __clz((int)t2);  // index of the top bit within T (t2 != 0)
+  const int base = 32 * (c0 + m - 2);   // weight exponent of T's bit 0 (may be negative)
+  const int P = base + top - 1;         // top bit of A / 2
+  if (P < 53) {
+    // A / 2 < 2^53: exactly representable, its bits are the value (subnormals
+    // and the lowest normal binade). With t2 != 0, T >= 2^64, so this needs
+    // base <= -32: the top digit is chunk 1 (A = t2:t1) or chunk 0 (A = t2).
+    const unsigned long long A = base == -32 ? (((unsigned long long)t2 << 32) | t1)
+                                             : (unsigned long long)t2;
+    return (A >> 1) | sign;
+  }
+  // 53 bits from A's top bit down: bits [top - 52, top] of T (top >= 64 since t2 != 0)
+  const int lsb = top - 52;  // >= 12
+  const unsigned long long hi64 = ((unsigned long long)t2 << 32) | t1;
+  // T = hi64 * 2^32 + t0; q = T >> lsb; rest = T mod 2^lsb; half = 2^(lsb - 1)
+  const unsigned long long q0 = lsb >= 32 ? hi64 >> (lsb - 32)
+                                          : (hi64 << (32 - lsb)) | ((unsigned long long)t0 >> lsb);
+  unsigned long long q = q0 & ((1ull << 53) - 1ull);
+  // rest and half, compared as (rest > half) / (rest == half); rest < 2^lsb <= 2^43
+  unsigned long long rest;
+  if (lsb >= 32) {
+    rest = ((hi64 & ((1ull << (lsb - 32)) - 1ull)) << 32) | t0;
+  } else {
+    rest = (unsigned long long)t0 & ((1ull << lsb) - 1ull);
+  }
+  const unsigned long long half = 1ull << (lsb - 1);
+  const bool up = rest > half || (rest == half && (low || (q & 1ull)));
+  int sh = P - 52;  // bits of A / 2 below q
+  q += up ? 1ull : 0ull;
+  if (q == (1ull << 53)) {
+    q >>= 1;
+    ++sh;
+  }
+  const int e = sh + 1;
+  if (e >= 2047) return kPosInf | sign;
+  return ((unsigned long long)(e - 1) << 52) + q + sign;
+}
+
 // Correctly rounded exact sum (ties to even) of an accumulator whose chunks
 // are spread over the warp as above.
 __device__ __noinline__ static unsigned long long warp_round(long long v0, long long v1,

@@ -428,14 +428,9 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
     // its own chunk c into the low 32 bits and the signed high part (owed to
     // chunk c + 1) and clears it; the 32-lane sums come from 32-bit warp
     // reductions of 16-bit digits (digit sums below 2^21 in magnitude: exact).
-    // Lane L collects chunks L, L + 32 and L + 64 of the sum.
-    long long v0 = 0, v1 = 0, v2 = 0;
-    auto put = [&](int k, long long val) {
-      if (k < 32) { if (lane == k) v0 += val; }
-      else if (k < 64) { if (lane == k - 32) v1 += val; }
-      else if (lane == k - 64) v2 += val;
-    };
-    for (int c = cmin; c <= cmax; ++c) {
+    const unsigned f = __reduce_or_sync(kFull, T.flags()) | kFlagAny;
+    const unsigned long long key = warp_max_ull(T.nkey);
+    auto chunk_sums = [&](int c, long long& sum_lo, long long& sum_hi) {
       const long long u = T.acc[c * BLOCK];
       T.acc[c * BLOCK] = 0;
       const unsigned lw = (unsigned)u;
@@ -444,17 +439,49 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
       const unsigned l1 = __reduce_add_sync(kFull, lw >> 16);
       const unsigned h0 = __reduce_add_sync(kFull, (unsigned)hw & 0xFFFFu);
       const int h1 = __reduce_add_sync(kFull, hw >> 16);
-      const long long sum_lo = (long long)l0 + (long long)l1 * 65536ll;
-      const long long sum_hi = (long long)h0 + (long long)h1 * 65536ll;
+      sum_lo = (long long)l0 + (long long)l1 * 65536ll;
+      sum_hi = (long long)h0 + (long long)h1 * 65536ll;
+    };
+    constexpr int kWin = 8;  // windows up to this many chunks round in one thread
+    if (cmax - cmin < kWin && cmax < kSChunks - 1) {
+      // the sums are the same in every lane: lane 0 rounds the window alone
+      long long w[kWin + 1];
+#pragma unroll
+      for (int k = 0; k <= kWin; ++k) w[k] = 0;
+#pragma unroll
+      for (int k = 0; k < kWin; ++k) {
+        if (cmin + k <= cmax) {
+          long long sl, shv;
+          chunk_sums(cmin + k, sl, shv);
+          w[k] += sl;
+          w[k + 1] += shv;
+        }
+      }
+      if (lane == 0) {
+        const int nw = cmax >= cmin ? cmax - cmin + 2 : 0;
+        reinterpret_cast<unsigned long long*>(a.out)[s] = round_window(w, nw, cmin, f, key);
+      }
+      __syncwarp();
+      continue;
+    }
+    // wider windows: lane L collects chunks L, L + 32 and L + 64 of the sum
+    // and the warp rounds
+    long long v0 = 0, v1 = 0, v2 = 0;
+    auto put = [&](int k, long long val) {
+      if (k < 32) { if (lane == k) v0 += val; }
+      else if (k < 64) { if (lane == k - 32) v1 += val; }
+      else if (lane == k - 64) v2 += val;
+    };
+    for (int c = cmin; c <= cmax; ++c) {
+      long long sl, shv;
+      chunk_sums(c, sl, shv);
       if (c == kSChunks - 1) {
-        put(c, sum_lo + sum_hi * 4294967296ll);
+        put(c, sl + shv * 4294967296ll);
       } else {
-        put(c, sum_lo);
-        put(c + 1, sum_hi);
+        put(c, sl);
+        put(c + 1, shv);
       }
     }
-    const unsigned f = __reduce_or_sync(kFull, T.flags()) | kFlagAny;
-    const unsigned long long key = warp_max_ull(T.nkey);
     __syncwarp();  // chunks 0..2 of the warp's threads are the rounding scratch now
     const unsigned long long r = warp_round(v0, v1, v2, f, key, smem_seg + warp * 32, BLOCK);
     if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;

@@ -163,3 +163,36 @@ def test_tiles_longer_than_the_carry_interval(tile):
                  {"block": 192, "unroll": 4, "tile_elems": tile, "short_max": 0}):
         got = run_plan(vd, od, lengths.size, opts)
         assert np.array_equal(got, expect), (opts, [hex(int(g)) for g in got], [hex(int(x)) for x in expect])
+
+
+def test_golden_boundary_cases_as_short_segments():
+    """Every hand-derived boundary case (ties to even, sticky bits from
+    2^-1074, overflow at the midpoint below 2^1024, subnormal results, signed
+    zeros, Inf/NaN rules) as one short segment, repeated with padding zeros and
+    with the terms scaled into other chunks: the one-thread rounding of small
+    windows and the warp rounding must both give the expected bits."""
+    from tests.test_oracle import GOLDEN_CASES
+    segs, expect = [], []
+    for name, bits, exp in GOLDEN_CASES:
+        segs.append(list(bits))
+        expect.append(exp)
+        if bits:  # the same case followed by zeros (+0 keeps -0 results -0 only if all are -0)
+            padded = list(bits) + [0x8000000000000000] * 40
+            segs.append(padded)
+            expect.append(c_oracle.sum_bits(np.array(padded, dtype=np.uint64)))
+    # windows of every width near the 8-chunk limit: one term per chunk
+    for width in range(1, 12):
+        bits = [int(np.array([2.0 ** (32 * k - 300) * (1 + k / 7)], dtype=np.float64).view(np.uint64)[0])
+                for k in range(width)]
+        bits.append(int(np.array([-(2.0 ** -300)], dtype=np.float64).view(np.uint64)[0]))
+        segs.append(bits)
+        expect.append(c_oracle.sum_bits(np.array(bits, dtype=np.uint64)))
+    lengths = np.array([len(x) for x in segs], dtype=np.int64)
+    off = W.cfg3_offsets(lengths)
+    flat = np.array([b for x in segs for b in x], dtype=np.uint64)
+    vd = to_device(flat if flat.size else np.zeros(1, dtype=np.uint64))
+    od = torch.from_numpy(off).cuda()
+    for opts in ({"block": 128, "unroll": 8, "short_max": 4096}, {"block": 192, "unroll": 4, "short_max": 64}):
+        got = run_plan(vd, od, lengths.size, opts)
+        bad = [(k, hex(int(got[k])), hex(int(expect[k]))) for k in range(lengths.size) if int(got[k]) != int(expect[k])]
+        assert not bad, (opts, bad[:5])
