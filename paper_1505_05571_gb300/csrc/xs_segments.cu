@@ -300,7 +300,17 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
       }, cmin, cmax);
       gsync();
       for (int c = cmin; c <= cmax; ++c) T.acc[c * BLOCK] = 0;
-      if (gwarp == 0) {
+      constexpr int kWin = 8;  // windows up to this many chunks round in one thread
+      if (cmax - cmin < kWin && cmax < kSChunks - 1) {
+        if (gt == 0) {
+          long long w[kWin + 1];
+#pragma unroll
+          for (int k = 0; k <= kWin; ++k) w[k] = cmin + k <= cmax + 1 ? bsum[cmin + k] : 0;
+          const int nw = cmax >= cmin ? cmax - cmin + 2 : 0;
+          reinterpret_cast<unsigned long long*>(a.out)[s] =
+              round_window(w, nw, cmin, s_flags | kFlagAny, s_nkey);
+        }
+      } else if (gwarp == 0) {
         const long long v0 = bsum[lane], v1 = bsum[lane + 32], v2 = lane < 3 ? bsum[lane + 64] : 0;
         __syncwarp();  // bsum is the rounding scratch from here on
         const unsigned long long r = warp_round(v0, v1, v2, s_flags | kFlagAny, s_nkey, bsum, 32);
