@@ -45,12 +45,20 @@ __device__ __forceinline__ void load_full(const Split& sp, long long t, int tid,
   for (int u = 0; u < UNROLL; ++u) buf[u] = ld_stream(p + u * BLOCK);
 }
 
-template <int BLOCK, int UNROLL>
+// TRACK (the shapes used below 2^25 values): each thread also keeps the range
+// of positional exponents its terms had, so a mode-0 sum merges only the
+// window of chunks they touched and, when it is narrow, rounds in one thread.
+template <int BLOCK, int UNROLL, bool TRACK>
 __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   extern __shared__ __align__(16) long long smem_small[];
+  __shared__ unsigned s_wmin, s_wmax;
   const int tid = threadIdx.x;
   SmallThread T;
   T.acc = smem_small + tid;
+  if (TRACK && tid == 0) {
+    s_wmin = 0x7FFu;
+    s_wmax = 0u;
+  }
 
   const Split sp = split_input(a.x, a.n);
   constexpr long long TP = (long long)BLOCK * UNROLL;
@@ -68,13 +76,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   if (t < nfull) load_full<BLOCK, UNROLL>(sp, t, tid, A);
   if (blockIdx.x == 0 && tid == 0) {
     const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
-    if (sp.head) T.one<BLOCK>(xb[0]);
-    if (sp.tail) T.one<BLOCK>(xb[a.n - 1]);
+    if (sp.head) T.one<BLOCK, TRACK>(xb[0]);
+    if (sp.tail) T.one<BLOCK, TRACK>(xb[a.n - 1]);
   }
   int since = 0;
   auto tick = [&]() {
     if (++since >= a.carry_tiles) {
       sacc_propagate(T.acc, BLOCK);
+      if (TRACK) T.emax = kWindowTop;  // carries may fill the chunks above
       since = 0;
     }
   };
@@ -83,25 +92,55 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   while (t < nfull) {
     if (tid == 0 && a.prefetch > 0) prefetch_tile<BLOCK, UNROLL>(sp, t + (a.prefetch + 1) * G, ntiles);
     if (t + G < nfull) load_full<BLOCK, UNROLL>(sp, t + G, tid, B);
-    T.group_spec<BLOCK, UNROLL>(A);
+    T.group_spec<BLOCK, UNROLL, TRACK>(A);
     tick();
     t += G;
     if (t >= nfull) break;
     if (tid == 0 && a.prefetch > 0) prefetch_tile<BLOCK, UNROLL>(sp, t + (a.prefetch + 1) * G, ntiles);
     if (t + G < nfull) load_full<BLOCK, UNROLL>(sp, t + G, tid, A);
-    T.group_spec<BLOCK, UNROLL>(B);
+    T.group_spec<BLOCK, UNROLL, TRACK>(B);
     tick();
     t += G;
   }
   // The ragged last tile (padded with -0, which adds nothing).
   if (t == nfull && nfull < ntiles) {
     load_tile<BLOCK, UNROLL>(sp, t, tid, A);
-    T.group_spec<BLOCK, UNROLL>(A);  // the -0 padding is taken back: once per launch
+    T.group_spec<BLOCK, UNROLL, TRACK>(A);  // the -0 padding is taken back: once per launch
   }
-  __syncthreads();
+  __syncthreads();  // also orders thread 0's window initialisation before the atomics below
   grid_launch_dependents();
+  if (TRACK && a.mode == 0) {
+    const unsigned wmin = __reduce_min_sync(kFull, T.emin);
+    const unsigned wmax = __reduce_max_sync(kFull, T.emax);
+    if ((tid & 31) == 0 && wmax >= wmin) {
+      atomicMin(&s_wmin, wmin);
+      atomicMax(&s_wmax, wmax);
+    }
+    __syncthreads();
+  }
   unsigned f = T.flags();
   if (blockIdx.x == 0 && tid == 0 && a.n > 0) f |= kFlagAny;
+  if (TRACK && a.mode == 0) {
+    const bool any = s_wmax >= s_wmin;
+    const int cmin = (int)(s_wmin >> kLowExpBits);
+    const int cmax = any ? (int)(s_wmax >> kLowExpBits) + 1 : cmin - 1;
+    unsigned long long* gch = reinterpret_cast<unsigned long long*>(a.g->chunk);
+    block_chunk_sums<BLOCK>(smem_small, [&](int c, long long v) {
+      if (v != 0) atomicAdd(gch + c, (unsigned long long)v);
+    }, cmin, min(cmax, kSChunks - 1));
+    f = __reduce_or_sync(kFull, f);
+    const unsigned long long key = warp_max_ull(T.nkey);
+    if ((tid & 31) == 0) {
+      if (f) atomicOr(&a.g->flags, f);
+      if (key) atomicMax(&a.g->nan_key, key);
+    }
+    if (tid == 0 && any) {
+      atomicMax(&a.g->win_lo_inv, 0x7FFu - s_wmin);
+      atomicMax(&a.g->win_hi, s_wmax);
+    }
+    finish_grid_window(a, smem_small);
+    return;
+  }
   block_small_to_global<BLOCK>(smem_small, a, f, T.nkey);
   finish_grid(a, smem_small);
 }
@@ -289,15 +328,16 @@ template <int B>
 constexpr size_t small_smem() { return (size_t)B * kSChunks * sizeof(long long); }
 
 const KernelEntry kKernels[] = {
-    {XS_METHOD_SMALL, 128, 4, k_sum_small<128, 4>, small_smem<128>()},
-    {XS_METHOD_SMALL, 128, 8, k_sum_small<128, 8>, small_smem<128>()},
-    {XS_METHOD_SMALL, 256, 4, k_sum_small<256, 4>, small_smem<256>()},
-    {XS_METHOD_SMALL, 256, 8, k_sum_small<256, 8>, small_smem<256>()},
-    {XS_METHOD_SMALL, 192, 4, k_sum_small<192, 4>, small_smem<192>()},
-    {XS_METHOD_SMALL, 192, 8, k_sum_small<192, 8>, small_smem<192>()},
-    {XS_METHOD_SMALL, 384, 4, k_sum_small<384, 4>, small_smem<384>()},
-    {XS_METHOD_SMALL, 384, 6, k_sum_small<384, 6>, small_smem<384>()},
-    {XS_METHOD_SMALL, 384, 8, k_sum_small<384, 8>, small_smem<384>()},
+    // the shapes chosen below 2^25 values track chunk windows (k_sum_small)
+    {XS_METHOD_SMALL, 128, 4, k_sum_small<128, 4, true>, small_smem<128>()},
+    {XS_METHOD_SMALL, 128, 8, k_sum_small<128, 8, false>, small_smem<128>()},
+    {XS_METHOD_SMALL, 256, 4, k_sum_small<256, 4, true>, small_smem<256>()},
+    {XS_METHOD_SMALL, 256, 8, k_sum_small<256, 8, false>, small_smem<256>()},
+    {XS_METHOD_SMALL, 192, 4, k_sum_small<192, 4, false>, small_smem<192>()},
+    {XS_METHOD_SMALL, 192, 8, k_sum_small<192, 8, false>, small_smem<192>()},
+    {XS_METHOD_SMALL, 384, 4, k_sum_small<384, 4, true>, small_smem<384>()},
+    {XS_METHOD_SMALL, 384, 6, k_sum_small<384, 6, false>, small_smem<384>()},
+    {XS_METHOD_SMALL, 384, 8, k_sum_small<384, 8, false>, small_smem<384>()},
     {XS_METHOD_LARGE, 256, 4, k_sum_large<256, 4>, sizeof(LargeSmem)},
     {XS_METHOD_LARGE, 256, 8, k_sum_large<256, 8>, sizeof(LargeSmem)},
     {XS_METHOD_LARGE, 128, 8, k_sum_large<128, 8>, sizeof(LargeSmem)},
@@ -477,7 +517,7 @@ xs_status launch_small_fixed(const double* d_values, int64_t n, AccState* target
   a.carry_tiles = std::max(1, (kCarryInterval - 2) / (2 * U));
   a.prefetch = prefetch_tiles(kSumPrefetch);
   a.divisor = 0ull;
-  k_sum_small<B, U><<<(unsigned)g, B, small_smem<B>(), s>>>(a);
+  k_sum_small<B, U, true><<<(unsigned)g, B, small_smem<B>(), s>>>(a);
   XS_TRY_CUDA(cudaGetLastError());
   return XS_OK;
 }
@@ -488,9 +528,9 @@ xs_status small_fixed_grid(int* grid) {
   int dev = 0, sms = 0, occ = 0;
   XS_TRY_CUDA(cudaGetDevice(&dev));
   XS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  XS_TRY_CUDA(cudaFuncSetAttribute(k_sum_small<384, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  XS_TRY_CUDA(cudaFuncSetAttribute(k_sum_small<384, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)small_smem<384>()));
-  XS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sum_small<384, 4>, 384,
+  XS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sum_small<384, 4, true>, 384,
                                                             small_smem<384>()));
   *grid = sms * (occ > 0 ? occ : 1);
   return XS_OK;

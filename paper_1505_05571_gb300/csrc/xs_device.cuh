@@ -53,7 +53,11 @@ struct __align__(16) AccState {
   unsigned flags;
   unsigned ticket;  // completion counter of the kernel writing into it; 0 at rest
   unsigned long long nan_key;  // 0 = no NaN seen
-  unsigned long long reserved;
+  // chunk window of a sum being rounded (kernels that track it, mode 0 only):
+  // max over blocks of 0x7FF - (lowest positional exponent) and of the
+  // highest; 0 and 0 = no finite nonzero term yet. 0 at rest.
+  unsigned win_lo_inv;
+  unsigned win_hi;
 };
 static_assert(sizeof(AccState) == 560, "AccState layout");
 

@@ -64,6 +64,65 @@ static __device__ void finish_grid(const SumArgs& a, long long* sc) {
   }
 }
 
+// Finish of a mode-0 sum whose blocks recorded their chunk window in g: when
+// the window holds at most 9 chunks (and no division follows) the last
+// block's thread 0 reads and clears just those and rounds alone
+// (round_window); otherwise the warp path.
+static __device__ void finish_grid_window(const SumArgs& a, long long* sc) {
+  __shared__ unsigned s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&a.g->ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x >= 32) return;
+  __threadfence();
+  const unsigned lo_inv = *(volatile unsigned*)&a.g->win_lo_inv;
+  const unsigned hi = *(volatile unsigned*)&a.g->win_hi;
+  const bool empty = lo_inv == 0u && hi == 0u;
+  // a term with positional exponent e touches chunks e >> 5 and (e >> 5) + 1,
+  // and the block merge carries each chunk's high part one chunk further up
+  const int cmin = empty ? 0 : (int)((0x7FFu - lo_inv) >> kLowExpBits);
+  const int cmax = empty ? -1 : min((int)(hi >> kLowExpBits) + 2, kSChunks - 1);  // highest written
+  constexpr int kWin = 8;
+  if (a.divisor == 0ull && cmax - cmin <= kWin) {
+    if (threadIdx.x != 0) return;
+    unsigned long long* ch = reinterpret_cast<unsigned long long*>(a.g->chunk);
+    long long w[kWin + 1];
+#pragma unroll
+    for (int k = 0; k <= kWin; ++k)
+      w[k] = cmin + k <= cmax ? (long long)atomicExch(ch + cmin + k, 0ull) : 0;
+    const unsigned flags = atomicExch(&a.g->flags, 0u);
+    const unsigned long long key = atomicExch(&a.g->nan_key, 0ull);
+    a.g->win_lo_inv = 0u;
+    a.g->win_hi = 0u;
+    atomicExch(&a.g->ticket, 0u);
+    *reinterpret_cast<unsigned long long*>(a.out) =
+        round_window(w, cmax - cmin + 1 > 0 ? cmax - cmin + 1 : 0, cmin, flags, key);
+    return;
+  }
+  const int lane = threadIdx.x;
+  unsigned long long* ch = reinterpret_cast<unsigned long long*>(a.g->chunk);
+  long long v0 = (long long)atomicExch(ch + lane, 0ull);
+  long long v1 = (long long)atomicExch(ch + lane + 32, 0ull);
+  long long v2 = lane < 3 ? (long long)atomicExch(ch + lane + 64, 0ull) : 0;
+  unsigned flags = 0u;
+  unsigned long long key = 0ull;
+  if (lane == 0) {
+    flags = atomicExch(&a.g->flags, 0u);
+    key = atomicExch(&a.g->nan_key, 0ull);
+    a.g->win_lo_inv = 0u;
+    a.g->win_hi = 0u;
+    atomicExch(&a.g->ticket, 0u);
+  }
+  flags = __shfl_sync(kFull, flags, 0);
+  key = __shfl_sync(kFull, key, 0);
+  const unsigned long long bits = a.divisor ? warp_round_div(v0, v1, v2, flags, key, a.divisor, sc, 32)
+                                            : warp_round(v0, v1, v2, flags, key, sc, 32);
+  if (lane == 0) *reinterpret_cast<unsigned long long*>(a.out) = bits;
+}
+
 // Split of the input into an optional unaligned head element, 16-byte pairs
 // and an optional tail element.
 struct Split {
