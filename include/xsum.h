@@ -220,7 +220,9 @@ typedef struct xs_seg_options {
   int unroll;        /* 16-byte loads per thread per tile */
   int tile_elems;    /* elements per block work item of a long segment */
   int short_max;     /* segments up to this length are summed by one warp */
-  int carry_tiles;   /* tiles between per-thread carry propagations */
+  int carry_tiles;   /* load groups (2 x unroll adds per thread each) between per-thread carry
+                        propagations inside a tile longer than 2040 values per thread; 0 gives
+                        the longest interval that keeps 2047 adds, larger values are rejected */
 } xs_seg_options;
 xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const int64_t* d_offsets,
                              int64_t nseg, double* d_out, const xs_seg_options* opts,

@@ -43,6 +43,7 @@ struct SegArgs {
   long long tile_cap;
   long long tile_elems;
   long long short_max;
+  int carry_groups;             // load groups between carry propagations in a tile (0: longest safe)
 };
 
 constexpr int kPrepThreads = 256;
@@ -274,7 +275,9 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
     if (t >= ntiles) break;
     const long long s = s_meta[0], lo = s_meta[1], hi = s_meta[2], seg_tiles = s_meta[3];
     T.reset();
-    accumulate_range<BLOCK, UNROLL, true, true>(T, a.x, lo, hi, gt, W, kCarryGroups);
+    accumulate_range<BLOCK, UNROLL, true, true>(T, a.x, lo, hi, gt, W,
+                                                a.carry_groups > 0 ? min(a.carry_groups, kCarryGroups)
+                                                                   : kCarryGroups);
     {
       const unsigned wmin = __reduce_min_sync(kFull, T.emin);
       const unsigned wmax = __reduce_max_sync(kFull, T.emax);
@@ -531,6 +534,10 @@ int find_seg(int block, int unroll) {
 
 size_t seg_smem(int block) { return (size_t)block * kSChunks * sizeof(long long); }
 
+// The longest interval, in load groups of 2 x unroll adds, between per-thread
+// carry propagations inside a tile (head, tail and the padded group included).
+int seg_max_carry_groups(int unroll) { return (kCarryInterval - 4 - 2 * unroll) / (2 * unroll); }
+
 xs_seg_options default_seg_options(DeviceCtx* ctx) {
   if (ctx->have_tuned_seg) return ctx->tuned_seg;
   xs_seg_options o;
@@ -554,8 +561,10 @@ xs_status resolve_options(DeviceCtx* ctx, const xs_seg_options* in, xs_seg_optio
   if (o.tile_elems == 0) o.tile_elems = d.tile_elems;
   if (o.short_max == 0) o.short_max = d.short_max;
   if (find_seg(o.block, o.unroll) < 0) return set_error(XS_ERR_NOT_SUPPORTED);
-  // tiles longer than 2040 values per thread propagate carries inside the tile
+  // tiles longer than 2040 values per thread propagate carries inside the tile,
+  // at most every seg_max_carry_groups(unroll) load groups
   if (o.tile_elems < 2 * o.block || o.tile_elems > (1 << 26)) return set_error(XS_ERR_INVALID_VALUE);
+  if (o.carry_tiles < 0 || o.carry_tiles > seg_max_carry_groups(o.unroll)) return set_error(XS_ERR_INVALID_VALUE);
   if (o.short_max < 0 || o.short_max > 2040 * 32) return set_error(XS_ERR_INVALID_VALUE);
   *out = o;
   return XS_OK;
@@ -680,6 +689,7 @@ xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const in
                                       bytes_blk);
   a.tile_cap = (long long)tile_cap;
   a.tile_elems = o.tile_elems;
+  a.carry_groups = o.carry_tiles;
   a.short_max = o.short_max;
   // capture prep + main into a graph on a private stream
   cudaStream_t cs;
@@ -769,14 +779,15 @@ xs_status xs_autotune_segments(const double* d_values, const int64_t* d_offsets,
   cudaStream_t s = as_stream(stream);
   std::vector<xs_seg_options> cands;
   const int blocks[][2] = {{128, 4}, {192, 4}, {256, 4}, {384, 4}, {192, 8}, {128, 8}};
-  const int tiles[] = {1 << 16, 1 << 17, 1 << 18};
+  const int tiles[] = {1 << 16, 1 << 17, 1 << 18, 1 << 20};
   const int shorts[] = {1024, 4096, 16384};
   for (auto& b : blocks)
     for (int t : tiles)
       for (int sm : shorts) {
-        xs_seg_options o{b[0], b[1], t, sm, 0};
-        if ((long long)t > 2040LL * b[0]) continue;
-        cands.push_back(o);
+        cands.push_back(xs_seg_options{b[0], b[1], t, sm, 0});
+        // tiles past 2040 values per thread propagate carries: try half the interval too
+        if ((long long)t > 2040LL * b[0])
+          cands.push_back(xs_seg_options{b[0], b[1], t, sm, seg_max_carry_groups(b[1]) / 2});
       }
   cudaEvent_t e0, e1;
   XS_TRY_CUDA(cudaEventCreate(&e0));

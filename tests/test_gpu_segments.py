@@ -160,9 +160,15 @@ def test_tiles_longer_than_the_carry_interval(tile):
     vd = to_device(vals)
     od = torch.from_numpy(off).cuda()
     for opts in ({"block": 128, "unroll": 8, "tile_elems": tile, "short_max": 64},
-                 {"block": 192, "unroll": 4, "tile_elems": tile, "short_max": 0}):
+                 {"block": 192, "unroll": 4, "tile_elems": tile, "short_max": 0},
+                 {"block": 128, "unroll": 8, "tile_elems": tile, "short_max": 64, "carry_tiles": 1},
+                 {"block": 192, "unroll": 4, "tile_elems": tile, "short_max": 64, "carry_tiles": 37}):
         got = run_plan(vd, od, lengths.size, opts)
         assert np.array_equal(got, expect), (opts, [hex(int(g)) for g in got], [hex(int(x)) for x in expect])
+    out = torch.empty(lengths.size, dtype=torch.float64, device="cuda")
+    with pytest.raises(xsum.XsError) as e:  # longer than 2047 adds between propagations
+        xsum.xs_seg_plan_create(vd, od, lengths.size, out, {"block": 128, "unroll": 8, "carry_tiles": 128})
+    assert e.value.status == xsum.XS_ERR_INVALID_VALUE
 
 
 def test_golden_boundary_cases_as_short_segments():
