@@ -8,7 +8,7 @@ steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the CPU oracle (plain C, one core) on the machine's host on
+--impl reference times the CPU oracle (plain C, one core) on the host CPU, on
 a bounded sample of the same workload. With N > 1 (torchrun) every rank sums
 its own replica of the workload on its own GPU (no collective on the data
 path); rank 0 prints the whole-job throughput over the slowest rank.
