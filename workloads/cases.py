@@ -2,7 +2,7 @@
 
     python -m workloads.cases <case> [--reps N] [--prefetch TILES]
 
-Cases: sum_cfg1, mean_cfg1, large_cfg1, dot_cfg1, norm2_cfg1, f32_2e8,
+Cases: sum_cfg1, sum_cfg2a (2^28 doubles, full exponent range), mean_cfg1, large_cfg1, dot_cfg1, norm2_cfg1, f32_2e8,
 seg_cfg3_5k (5,000 segments of the config-3 length law), seg_tiny (2,000,000
 segments of 1..100 values). Inputs are generated on the device; the case prints
 its median CUDA-event time. This module only calls the library.
@@ -28,6 +28,11 @@ def build_case(name: str):
 
     dev = torch.device("cuda", 0)
     out = torch.empty(1, dtype=torch.float64, device=dev)
+    if name == "sum_cfg2a":  # exponents uniform over the full range, subnormals included
+        n = 1 << 28
+        x = torch.empty(n, dtype=torch.int64, device=dev)
+        devgen.full_range(x, 0, 0)
+        return (lambda: xsum.xs_sum_async(x.view(torch.float64), n, out)), 8 * n, (x,)
     if name in ("sum_cfg1", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1"):
         n = 10 ** 8
         x = torch.empty(n, dtype=torch.int64, device=dev)
