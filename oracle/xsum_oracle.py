@@ -230,10 +230,6 @@ def segment_sums_bits(bits, offsets) -> list[int]:
     return [sum_bits(bits[int(offsets[k]):int(offsets[k + 1])]) for k in range(len(offsets) - 1)]
 
 
-def _u64(x: int) -> int:
-    return x & ((1 << 64) - 1)
-
-
 def canonical_chunks(st: ExactState) -> list[int]:
     """The value as the paper's 67 normalised chunks (small-superaccumulator form).
 

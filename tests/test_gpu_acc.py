@@ -6,7 +6,6 @@ split, sum parts exactly, add the superaccumulators, round once).
 
 import numpy as np
 import pytest
-import torch
 
 import workloads as W
 from oracle import c_oracle

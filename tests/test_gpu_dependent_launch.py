@@ -4,9 +4,7 @@ before it finishes. A sum whose input holds the previous sum's result (written
 by the previous grid's last block) must see that result, and sums that share
 the stream's workspace accumulator must not mix."""
 
-import numpy as np
 import pytest
-import torch
 
 import workloads as W
 from oracle import c_oracle, products

@@ -3,7 +3,6 @@ accumulator by any positive integer) against the oracle, bit for bit."""
 
 import numpy as np
 import pytest
-import torch
 
 import workloads as W
 from oracle import c_oracle

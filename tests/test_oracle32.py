@@ -5,7 +5,6 @@ import itertools
 import numpy as np
 import pytest
 
-import workloads as W
 from oracle import c_oracle
 from oracle import xsum_oracle32 as xo32
 

@@ -12,7 +12,7 @@ import pytest
 import workloads as W
 from oracle import c_oracle
 from oracle import xsum_oracle as xo
-from tests.test_oracle import EDGE, SMALL_GRID, b2f, f2b
+from tests.test_oracle import EDGE, SMALL_GRID, f2b
 
 DMAX = 1.7976931348623157e308
 

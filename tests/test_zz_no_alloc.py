@@ -9,9 +9,7 @@ failure has run every other test first; it also passes alone in a fresh
 process.
 """
 
-import numpy as np
 import pytest
-import torch
 
 import workloads as W
 from paper_1505_05571_gb300 import xsum
