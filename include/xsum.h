@@ -215,11 +215,15 @@ xs_status xs_sum_segments(const double* d_values, const int64_t* d_offsets, int6
 typedef struct xs_seg_plan_s* xs_seg_plan;
 /* Tunables of the segmented kernel; zero fields take the tuned or default value. */
 typedef struct xs_seg_options {
-  int block;         /* threads per work group of a long-segment tile (128, 192, 256 or 384;
-                        groups of 128 and 192 run three or two to one 384-thread block) */
-  int unroll;        /* 16-byte loads per thread per tile */
-  int tile_elems;    /* elements per block work item of a long segment */
-  int short_max;     /* segments up to this length are summed by one warp */
+  int block;         /* threads per work group of a long-segment tile: 128, 192, 256 or 384
+                        with unroll 4; 32, 64, 128 or 192 with unroll 8. Groups smaller than
+                        384 threads share one 384-thread block (twelve groups of one warp,
+                        six of two, three of 128, two of 192); default 32, one warp */
+  int unroll;        /* 16-byte loads per thread per load group; default 8 */
+  int tile_elems;    /* elements per work item of a long segment (2 x block .. 2^26);
+                        default 2^15 */
+  int short_max;     /* segments up to this length (at most 65,280) are summed by one warp;
+                        default 4096 */
   int carry_tiles;   /* load groups (2 x unroll adds per thread each) between per-thread carry
                         propagations inside a tile longer than 2040 values per thread; 0 gives
                         the longest interval that keeps 2047 adds, larger values are rejected */

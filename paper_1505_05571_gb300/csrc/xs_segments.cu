@@ -200,7 +200,10 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
   // groups of adds between carry propagations in a tile: with the head, tail
   // and padded last group, at most 2045 adds per thread
   constexpr int kCarryGroups = (kCarryInterval - 4 - 2 * UNROLL) / (2 * UNROLL);
-  static_assert(W >= 96 && W % 32 == 0, "warp 1 of a group claims the next tile; 67 chunk sums");
+  static_assert(W >= 32 && W % 32 == 0 && W <= 384, "whole warps, one block at most");
+  // the thread that claims the next tile: warp 1 of the group, beside warp 0's
+  // rounding; lane 0 when the group is one warp
+  constexpr int kClaimer = W > 32 ? 32 : 0;
   extern __shared__ __align__(16) long long smem_seg[];
   __shared__ long long g_bsum[NG][kSChunks];
   __shared__ long long g_item[NG];
@@ -217,9 +220,11 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
   unsigned& s_emin = g_emin[grp];
   unsigned& s_emax = g_emax[grp];
   unsigned long long& s_nkey = g_nkey[grp];
-  // barrier of the group's W threads (named barrier 1 + group)
+  // barrier of the group's W threads (named barrier 1 + group; a warp's own
+  // barrier when the group is one warp)
   auto gsync = [&]() {
-    if (NG == 1) __syncthreads();
+    if (W == 32) __syncwarp();
+    else if (NG == 1) __syncthreads();
     else asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(W) : "memory");
   };
   SmallThread T;
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
       }
     }
     gsync();  // every thread has read s_item; the window is complete
-    if (gt == 32) s_item = (long long)atomicAdd(&a.counters[2], 1ull);
+    if (gt == kClaimer) s_item = (long long)atomicAdd(&a.counters[2], 1ull);
     const int cmin = (int)(s_emin >> kLowExpBits);
     const int cmax = s_emax >= s_emin ? (int)(s_emax >> kLowExpBits) + 1 : cmin - 1;  // empty
     unsigned f = __reduce_or_sync(kFull, T.flags());
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
         if (lane == 0) reinterpret_cast<unsigned long long*>(a.out)[s] = r;
       }
     }
-    if (gt == 32) {  // the next tile: where it lies, and its first groups into L2
+    if (gt == kClaimer) {  // the next tile: where it lies, and its first groups into L2
       const long long tn = s_item;  // beside warp 0's rounding
       if (tn < ntiles) {
         describe(tn);
@@ -523,6 +528,8 @@ const SegEntry kSeg[] = {
     {384, 4, k_seg_main<384, 4>, SegShape<384>::block},
     {192, 8, k_seg_main<192, 8>, SegShape<192>::block},
     {128, 8, k_seg_main<128, 8>, SegShape<128>::block},
+    {64, 8, k_seg_main<64, 8>, SegShape<64>::block},
+    {32, 8, k_seg_main<32, 8>, SegShape<32>::block},
 };
 constexpr int kNumSeg = sizeof(kSeg) / sizeof(kSeg[0]);
 
@@ -541,13 +548,15 @@ int seg_max_carry_groups(int unroll) { return (kCarryInterval - 4 - 2 * unroll) 
 xs_seg_options default_seg_options(DeviceCtx* ctx) {
   if (ctx->have_tuned_seg) return ctx->tuned_seg;
   xs_seg_options o;
-  // measured on GB300 over the config-3 length law (100,000 segments):
-  // groups of 128 x 8 with tiles of 2^17 values 11.33 ms, 192 x 8 11.53 ms,
-  // 192 x 4 12.25 ms; uniform 10^4-value segments favour 128 x 4 --
-  // xs_autotune_segments picks per workload
-  o.block = 128;
+  // measured on GB300 over the config-3 length law (100,000 segments, 58 GB):
+  // one-warp groups of 32 x 8 with tiles of 2^15 values 10.09 ms, 64 x 8 with
+  // 2^16 10.85 ms, 128 x 8 with 2^17 11.11 ms, 192 x 8 11.53 ms. Independent
+  // warps end their tiles without waiting for one another; uniform segments of
+  // 10^7 values favour 128 x 8 (5.4 against 5.2 TB/s) -- xs_autotune_segments
+  // picks per workload
+  o.block = 32;
   o.unroll = 8;
-  o.tile_elems = 1 << 17;
+  o.tile_elems = 1 << 15;
   o.short_max = 4096;
   o.carry_tiles = 0;
   return o;
@@ -778,7 +787,7 @@ xs_status xs_autotune_segments(const double* d_values, const int64_t* d_offsets,
   if (!ctx) return st;
   cudaStream_t s = as_stream(stream);
   std::vector<xs_seg_options> cands;
-  const int blocks[][2] = {{128, 4}, {192, 4}, {256, 4}, {384, 4}, {192, 8}, {128, 8}};
+  const int blocks[][2] = {{128, 4}, {192, 4}, {256, 4}, {384, 4}, {192, 8}, {128, 8}, {64, 8}, {32, 8}};
   const int tiles[] = {1 << 16, 1 << 17, 1 << 18, 1 << 20};
   const int shorts[] = {1024, 4096, 16384};
   for (auto& b : blocks)

@@ -5,6 +5,7 @@ by the previous grid's last block) must see that result, and sums that share
 the stream's workspace accumulator must not mix."""
 
 import pytest
+import torch
 
 import workloads as W
 from oracle import c_oracle, products

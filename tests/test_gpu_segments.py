@@ -20,6 +20,9 @@ OPTS = [
     {"block": 384, "unroll": 4, "tile_elems": 1 << 18, "short_max": 16384},
     {"block": 192, "unroll": 8, "tile_elems": 3000, "short_max": 0},
     {"block": 128, "unroll": 8, "tile_elems": 1 << 14, "short_max": 256},
+    {"block": 64, "unroll": 8, "tile_elems": 1 << 15, "short_max": 4096},
+    {"block": 32, "unroll": 8, "tile_elems": 5000, "short_max": 128},
+    {"block": 32, "unroll": 8, "tile_elems": 1 << 17, "short_max": 0},
 ]
 
 
@@ -162,7 +165,8 @@ def test_tiles_longer_than_the_carry_interval(tile):
     for opts in ({"block": 128, "unroll": 8, "tile_elems": tile, "short_max": 64},
                  {"block": 192, "unroll": 4, "tile_elems": tile, "short_max": 0},
                  {"block": 128, "unroll": 8, "tile_elems": tile, "short_max": 64, "carry_tiles": 1},
-                 {"block": 192, "unroll": 4, "tile_elems": tile, "short_max": 64, "carry_tiles": 37}):
+                 {"block": 192, "unroll": 4, "tile_elems": tile, "short_max": 64, "carry_tiles": 37},
+                 {"block": 32, "unroll": 8, "tile_elems": tile, "short_max": 64}):
         got = run_plan(vd, od, lengths.size, opts)
         assert np.array_equal(got, expect), (opts, [hex(int(g)) for g in got], [hex(int(x)) for x in expect])
     out = torch.empty(lengths.size, dtype=torch.float64, device="cuda")
