@@ -264,7 +264,7 @@ typedef struct xs_server_options {
   int max_sessions;     /* accumulator slots, shared by sessions and one-shot sums (0 = 4096) */
   int streams;          /* batches in flight at once (0 = 3) */
   int max_batch;        /* requests per batch launch (0 = 256) */
-  int tile_elems;       /* elements per block work item (0 = 262144) */
+  int tile_elems;       /* elements per work item of a one-warp group (64 .. 2^26; 0 = 65536) */
 } xs_server_options;
 
 /* xs_request.flags */
