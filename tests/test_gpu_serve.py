@@ -153,3 +153,37 @@ def test_wait_times_out_on_the_host():
     for r in [rid] + rids:
         assert f2b(xsum.xs_server_wait(server, r)["value"]) == c_oracle.sum_bits(x)
     xsum.xs_server_destroy(server)
+
+
+@pytest.mark.parametrize("tile", [64, 3000, 1 << 20])
+def test_tile_sizes_and_carries_inside_a_tile(tile):
+    """The smallest tile (64 values), an odd size, and tiles of 2^20 values,
+    32,768 adds per thread of a one-warp group, where carries propagate inside
+    the tile. Same-sign terms at the top of a chunk (the largest adds), a
+    negative stretch (carries ripple as 2^32 - 1 chunks), zeros; a one-shot
+    sum, a negative one and a two-part session."""
+    rng = np.random.default_rng(tile)
+    n = 3_000_017
+    e = np.uint64(0x7DF)  # exponent 2015: chunk 62, shift 31
+    x = (e << np.uint64(52)) | rng.integers(0, 1 << 52, n, dtype=np.uint64)
+    x[1_000_000:2_000_000] |= np.uint64(1 << 63)
+    x[rng.integers(0, n, 5000)] = 0
+    d = to_device(x)
+    server = xsum.xs_server_create(streams=2, tile_elems=tile)
+    r_all = xsum.xs_server_submit(server, d, n)
+    r_neg = xsum.xs_server_submit(server, d[1_000_000:2_000_000], 1_000_000)
+    sid = xsum.xs_server_open_session(server)
+    xsum.xs_server_submit(server, d[:1_500_000], 1_500_000, session=sid)
+    r_s = xsum.xs_server_submit(server, d[1_500_000:], n - 1_500_000, session=sid,
+                                flags=xsum.XS_REQ_FINISH)
+    got = [f2b(xsum.xs_server_wait(server, r, 60_000_000_000)["value"]) for r in (r_all, r_neg, r_s)]
+    xsum.xs_server_destroy(server)
+    full = c_oracle.sum_bits(x)
+    assert got == [full, c_oracle.sum_bits(x[1_000_000:2_000_000]), full]
+
+
+def test_tile_size_limits():
+    for bad in (-5, 32, 63, 1 << 27):
+        with pytest.raises(xsum.XsError) as e:
+            xsum.xs_server_create(tile_elems=bad)
+        assert e.value.status == xsum.XS_ERR_INVALID_VALUE
