@@ -62,20 +62,26 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text: str) -> str:
+    """Source text without // comments and blank lines (comments do not change a kernel)."""
+    lines = (ln.split("//", 1)[0].rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_source_hash(kernel: str) -> str:
-    """Hash of the sources of one kernel; a profile taken on other sources is stale."""
+    """Hash of the code of one kernel; a profile taken on other code is stale."""
     csrc = os.path.join(ROOT, "paper_1505_05571_gb300", "csrc")
     h = hashlib.sha256()
-    with open(os.path.join(csrc, "xs_device.cuh"), "rb") as fh:
-        h.update(fh.read())
+    with open(os.path.join(csrc, "xs_device.cuh")) as fh:
+        h.update(_code_only(fh.read()).encode())
     for f, start, end in KERNEL_SOURCES[kernel]:
         with open(os.path.join(csrc, f)) as fh:
             text = fh.read()
         if start is None:
-            h.update(text.encode())
+            h.update(_code_only(text).encode())
             continue
         i = text.index(start)
-        h.update(text[i:text.index(end, i + len(start))].encode())
+        h.update(_code_only(text[i:text.index(end, i + len(start))]).encode())
     return h.hexdigest()[:16]
 
 

@@ -4,15 +4,16 @@
 // rounding). Work decomposition, computed on the device from the offsets by
 // k_seg_count / k_seg_scan / k_seg_fill:
 //   * long segments (length > short_max) are cut into tiles of tile_elems
-//     elements; a block sums a tile with per-thread small superaccumulators
-//     (Fig. 3). A one-tile segment is rounded by that block; the tiles of a
-//     longer segment meet in a per-segment global accumulator through integer
-//     atomics (partial superaccumulators added exactly, Discussion) and the
-//     last tile to finish rounds;
+//     elements; a work group (one warp by default, up to a block) sums a tile
+//     with per-thread small superaccumulators (Fig. 3). A one-tile segment is
+//     rounded by that group; the tiles of a longer segment meet in a
+//     per-segment global accumulator through integer atomics (partial
+//     superaccumulators added exactly, Discussion) and the last tile to finish
+//     rounds;
 //   * short segments are summed by one warp each; segments of at most two
 //     finite terms take a single IEEE addition, which is correctly rounded for
 //     two terms (Discussion).
-// Blocks take long tiles from a global cursor first, then their warps take
+// Groups take long tiles from a global cursor first, then their warps take
 // short segments from a second cursor, so short work fills the tail.
 #include <cuda_runtime.h>
 
