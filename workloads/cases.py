@@ -19,7 +19,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+CASES = ("sum_cfg1", "sum_cfg2a", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1", "f32_2e8",
+         "seg_cfg3_5k", "seg_tiny")
+
+
 def build_case(name: str):
+    if name not in CASES:
+        raise SystemExit(f"unknown case {name}")
     import numpy as np
     import torch
 
@@ -80,7 +86,7 @@ def main():
     import torch
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case")
+    ap.add_argument("case", choices=CASES)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--prefetch", type=int, default=None,
                     help="L2 prefetch distance in tiles (library default if absent)")
