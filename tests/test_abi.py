@@ -89,3 +89,40 @@ def test_prefetch_setting_range(lib_path):
             xsum.xs_set_prefetch_tiles(bad)
     for ok in (0, 5, 64, -1):
         xsum.xs_set_prefetch_tiles(ok)
+
+
+def test_argument_errors_come_before_any_device_work(lib_path):
+    """The documented error contract of the boundary, for arguments the host can
+    judge alone: it holds with or without a GPU, since no device call is made."""
+    import math
+
+    from paper_1505_05571_gb300 import xsum
+
+    def status_of(fn):
+        try:
+            fn()
+        except xsum.XsError as e:
+            return e.status
+        return xsum.XS_OK
+
+    E_VAL, E_PTR = xsum.XS_ERR_INVALID_VALUE, xsum.XS_ERR_INVALID_POINTER
+    cases = [
+        (lambda: xsum.xs_sum_ex(0x1000, -1), E_VAL),            # n < 0
+        (lambda: xsum.xs_sum_ex(0x1001, 10), E_VAL),            # not 8-byte aligned
+        (lambda: xsum.xs_sum_ex(0, 10), E_PTR),                 # null values
+        (lambda: xsum.xs_sum_host(0x1000, -3), E_VAL),
+        (lambda: xsum.xs_sum_host(0, 5), E_PTR),
+        (lambda: xsum.xs_sum_host(0x1004, 5), E_VAL),
+        (lambda: xsum.xs_sum_segments(0x1000, 0x2000, -1, 0x3000), E_VAL),
+        (lambda: xsum.xs_acc_add(0, 0x1000, 10), E_PTR),        # null handle
+        (lambda: xsum.xs_sum_f32_async(0x1000, -1, 0x2000), E_VAL),
+        (lambda: xsum.xs_sum_f32_async(0x1000, (1 << 39) + 1, 0x2000), E_VAL),
+    ]
+    for k, (fn, want) in enumerate(cases):
+        assert status_of(fn) == want, k
+    # empty inputs need no device either: +0 (the empty sum) and a no-op
+    assert xsum.xs_sum_ex(0x1000, 0) == 0.0 and math.copysign(1.0, xsum.xs_sum_ex(0, 0)) == 1.0
+    assert xsum.xs_sum_host(0, 0) == 0.0
+    xsum.xs_sum_segments(0x1000, 0x2000, 0, 0x3000)
+    # the blocking form reports through a quiet NaN and the thread's last error
+    assert math.isnan(xsum.xs_sum(0x1000, -1)) and xsum.xs_get_last_error() == E_VAL
