@@ -282,6 +282,23 @@ def med_time(torch, stream, fn, reps=20, warm=3):
     return ts[len(ts) // 2]
 
 
+def b2b_time(torch, stream, fn, calls=20, groups=5, warm=3):
+    """Per-call time (ms) of fn called back to back on `stream`: the median over
+    `groups` of the CUDA-event time of `calls` consecutive calls, divided by `calls`."""
+    for _ in range(warm):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(groups)]
+    for a, b in ev:
+        a.record(stream)
+        for _ in range(calls):
+            fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ts = sorted(a.elapsed_time(b) / calls for a, b in ev)
+    return ts[len(ts) // 2]
+
+
 def extra_configs(torch, np, xsum, devgen, W, dev, stream, rate_gbs, xd, n):
     """The other configurations, measured outside the headline's timed region."""
     out = {}
@@ -368,20 +385,20 @@ def extra_configs(torch, np, xsum, devgen, W, dev, stream, rate_gbs, xd, n):
 def next_rows(torch, np, xsum, devgen, dev, stream, xd, n):
     """Exact mean, dot product, squared norm, binary32 sum and tiny segments, each
     beside the inexact device routine that computes the same quantity."""
-    r = {}
+    r = {"timing": "per call, back to back: median over 5 groups of 20 consecutive calls"}
     res = torch.empty(1, dtype=torch.float64, device=dev)
     gbs = lambda b, ms: round(b / (ms * 1e-3) / 1e9, 1)  # noqa: E731
-    t = med_time(torch, stream, lambda: xsum.xs_mean_async(xd, n, res, stream), reps=10)
+    t = b2b_time(torch, stream, lambda: xsum.xs_mean_async(xd, n, res, stream))
     r["mean_cfg1"] = {"us": round(t * 1000, 1), "gbs": gbs(8 * n, t)}
     y = torch.empty(n, dtype=torch.int64, device=dev)
     devgen.band(y, 1, 0)
     yd = y.view(torch.float64)
-    t = med_time(torch, stream, lambda: xsum.xs_dot_async(xd, yd, n, res, stream), reps=10)
-    ti = med_time(torch, stream, lambda: torch.dot(xd, yd), reps=10)
+    t = b2b_time(torch, stream, lambda: xsum.xs_dot_async(xd, yd, n, res, stream))
+    ti = b2b_time(torch, stream, lambda: torch.dot(xd, yd))
     r["dot_cfg1"] = {"us": round(t * 1000, 1), "gbs": gbs(16 * n, t),
                      "inexact_torch_dot_us": round(ti * 1000, 1)}
-    t = med_time(torch, stream, lambda: xsum.xs_norm2_async(xd, n, res, stream), reps=10)
-    ti = med_time(torch, stream, lambda: torch.dot(xd, xd), reps=10)
+    t = b2b_time(torch, stream, lambda: xsum.xs_norm2_async(xd, n, res, stream))
+    ti = b2b_time(torch, stream, lambda: torch.dot(xd, xd))
     r["norm2_cfg1"] = {"us": round(t * 1000, 1), "gbs": gbs(8 * n, t),
                        "inexact_torch_dot_us": round(ti * 1000, 1),
                        "bound": "fp64 multiply pipe (0.53 T/s measured: 189 us for 1e8 products)"}
@@ -393,8 +410,8 @@ def next_rows(torch, np, xsum, devgen, dev, stream, xd, n):
          | (rng.integers(0, 2, m, dtype=np.uint32) << np.uint32(31)))
     f = torch.from_numpy(h.view(np.int32)).to(dev).view(torch.float32)
     o32 = torch.empty(1, dtype=torch.float32, device=dev)
-    t = med_time(torch, stream, lambda: xsum.xs_sum_f32_async(f, m, o32, stream), reps=10)
-    ti = med_time(torch, stream, lambda: torch.sum(f), reps=10)
+    t = b2b_time(torch, stream, lambda: xsum.xs_sum_f32_async(f, m, o32, stream))
+    ti = b2b_time(torch, stream, lambda: torch.sum(f))
     r["f32_2e8"] = {"us": round(t * 1000, 1), "gbs": gbs(4 * m, t),
                     "inexact_torch_sum_us": round(ti * 1000, 1)}
     del f
