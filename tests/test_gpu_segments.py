@@ -206,3 +206,33 @@ def test_golden_boundary_cases_as_short_segments():
         got = run_plan(vd, od, lengths.size, opts)
         bad = [(k, hex(int(got[k])), hex(int(expect[k]))) for k in range(lengths.size) if int(got[k]) != int(expect[k])]
         assert not bad, (opts, bad[:5])
+
+
+@pytest.mark.parametrize("block,unroll", [(32, 8), (128, 8)])
+def test_offsets_rewritten_in_place_past_the_tile_table(block, unroll):
+    """A plan replays over the offsets as they are at launch. Rewritten in place
+    to many more tiles than the plan's tile table holds, the tiles find their
+    segment by a binary search over the tile prefix sums (short segments, with
+    no tiles, sit between long ones)."""
+    nseg = 40
+    small = np.full(nseg, 10, dtype=np.int64)
+    big = W.cfg3_lengths(9, nseg, 200_000)
+    big[::7] = 3
+    off_small, off_big = W.cfg3_offsets(small), W.cfg3_offsets(big)
+    vals = W.cfg3_values(9, 0, int(off_big[-1]))
+    vd = to_device(vals)
+    od = torch.from_numpy(off_small).cuda()
+    out = torch.full((nseg,), float("nan"), dtype=torch.float64, device="cuda")
+    p = xsum.xs_seg_plan_create(vd, od, nseg, out,
+                                {"block": block, "unroll": unroll, "tile_elems": 4096, "short_max": 64})
+    try:
+        xsum.xs_seg_plan_launch(p)
+        torch.cuda.synchronize()
+        assert np.array_equal(bits_of(out), c_oracle.segment_sums_bits(vals, off_small))
+        od.copy_(torch.from_numpy(off_big))
+        out.fill_(float("nan"))
+        xsum.xs_seg_plan_launch(p)
+        torch.cuda.synchronize()
+        assert np.array_equal(bits_of(out), c_oracle.segment_sums_bits(vals, off_big))
+    finally:
+        xsum.xs_seg_plan_destroy(p)
