@@ -55,7 +55,8 @@ KERNEL_SOURCES = {
                     PREFETCH_DEFAULTS],
     "k_sum_large": [DEVICE_BLOCKS, ("xs_kernels.cuh", None, None),
                     ("xs_core.cu", "// Large superaccumulator kernel", "// Accumulator-handle kernels")],
-    "k_seg_main": [DEVICE_BLOCKS, ("xs_segments.cu", None, None)],
+    "k_seg_main": [DEVICE_BLOCKS, ("xs_segments.cu", "struct SegArgs {", "\nnamespace {"),
+                   ("xs_segments.cu", "xs_seg_options default_seg_options(", "xs_status resolve_options(")],
     "k_dot_small": [DEVICE_BLOCKS, ("xs_kernels.cuh", None, None), ("xs_dot.cu", None, None),
                     PREFETCH_DEFAULTS],
     "k_sum_f32": [DEVICE_BLOCKS, ("xs_f32.cu", None, None), PREFETCH_DEFAULTS],

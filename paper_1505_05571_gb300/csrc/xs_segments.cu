@@ -789,7 +789,7 @@ xs_status xs_autotune_segments(const double* d_values, const int64_t* d_offsets,
   cudaStream_t s = as_stream(stream);
   std::vector<xs_seg_options> cands;
   const int blocks[][2] = {{128, 4}, {192, 4}, {256, 4}, {384, 4}, {192, 8}, {128, 8}, {64, 8}, {32, 8}};
-  const int tiles[] = {1 << 16, 1 << 17, 1 << 18, 1 << 20};
+  const int tiles[] = {1 << 15, 1 << 16, 1 << 17, 1 << 18, 1 << 20};
   const int shorts[] = {1024, 4096, 16384};
   for (auto& b : blocks)
     for (int t : tiles)
