@@ -353,10 +353,17 @@ def extra_configs(torch, np, xsum, devgen, W, dev, stream, rate_gbs, xd, n):
         vd = v.view(torch.float64)
         od = torch.from_numpy(off).to(dev)
         so = torch.empty(nseg, dtype=torch.float64, device=dev)
-        plan = xsum.xs_seg_plan_create(vd, od, nseg, so, None, stream)
+        tuned = xsum.xs_autotune_segments(vd, od, nseg, so, reps=1, stream=stream)
+        plan = xsum.xs_seg_plan_create(vd, od, nseg, so, None, stream)  # the tuned options
+        launches = xsum.xs_seg_plan_kernel_launches(plan)
         t_seg = med_time(torch, stream, lambda: xsum.xs_seg_plan_launch(plan, stream), reps=10)
-        xsum.xs_seg_plan_destroy(plan)
         ref = so.clone()
+        xsum.xs_seg_plan_destroy(plan)
+        # one launch per segment: a C loop inside the library (xs_sum_each_async),
+        # then the same loop driven from Python (interpreter and ctypes cost included)
+        t_c = med_time(torch, stream, lambda: xsum.xs_sum_each_async(vd, off, nseg, so, stream), reps=3,
+                       warm=1)
+        same_c = bool(torch.equal(ref.view(torch.int64), so.view(torch.int64)))
         lib = xsum.load()
         base, ob, offs = vd.data_ptr(), so.data_ptr(), off.tolist()
         torch.cuda.synchronize(dev)
@@ -368,10 +375,13 @@ def extra_configs(torch, np, xsum, devgen, W, dev, stream, rate_gbs, xd, n):
         out["cfg3_segmented"] = {
             "segments": nseg, "values": total, "gb": round(total * 8 / 1e9, 2),
             "ms": round(t_seg, 3), "gbs": round(total * 8 / (t_seg * 1e-3) / 1e9, 1),
-            "kernel_launches_per_call": 4, "graph": True,
-            "one_launch_per_segment_ms": round(t_loop * 1000, 1),
-            "speedup_vs_one_launch_per_segment": round(t_loop * 1000 / t_seg, 1),
-            "same_bits_as_one_launch_per_segment": bool(torch.equal(ref.view(torch.int64), so.view(torch.int64))),
+            "autotuned_options": {k: v for k, v in tuned.items() if k != "us"},
+            "kernel_launches_per_call": launches, "graph": True,
+            "one_launch_per_segment_c_loop_ms": round(t_c, 1),
+            "speedup_vs_one_launch_per_segment": round(t_c / t_seg, 1),
+            "one_launch_per_segment_python_loop_ms": round(t_loop * 1000, 1),
+            "same_bits_as_one_launch_per_segment": same_c
+            and bool(torch.equal(ref.view(torch.int64), so.view(torch.int64))),
         }
         del v, vd
         torch.cuda.empty_cache()
@@ -498,9 +508,16 @@ def serving_report(torch, np, xsum, devgen, dev, stream, rate_gbs, n_arrivals=40
                            "arrivals_per_s": round(n_arrivals / span, 1), "batches": stats["batches"],
                            "p50_ms": round(float(np.percentile(lat, 50)), 3),
                            "p99_ms": round(float(np.percentile(lat, 99)), 3)}
-    # serial one-at-a-time through the plain API (also the "alone" result of each arrival)
+    # serial one at a time, each request alone: a C loop inside the library
+    # (xs_serial_replay), then the same loop driven from Python (labelled)
+    _, items, last_idx = trace(None)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    vals, _ = xsum.xs_serial_replay(items, stream)
+    t_serial_c = time.perf_counter() - t0
+    key = lambda v: int(np.array([v]).view(np.int64)[0])  # noqa: E731
+    same = all(key(vals[i]) == key(r["value"]) for i, r in zip(last_idx, res))
     out1 = torch.empty(1, dtype=torch.float64, device=dev)
-    same = True
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for a, r in zip(arrivals, res):
@@ -515,10 +532,14 @@ def serving_report(torch, np, xsum, devgen, dev, stream, rate_gbs, n_arrivals=40
         v = out1.item()
         if len(a) > 1:
             xsum.xs_acc_destroy(h)
-        same = same and (np.array([v]).view(np.int64)[0] == np.array([r["value"]]).view(np.int64)[0])
+        same = same and key(v) == key(r["value"])
     t_serial = time.perf_counter() - t0
-    report["serial_one_at_a_time"] = {"gbs": round(total_bytes / t_serial / 1e9, 1),
-                                      "arrivals_per_s": round(n_arrivals / t_serial, 1)}
+    report["serial_one_at_a_time"] = {"gbs": round(total_bytes / t_serial_c / 1e9, 1),
+                                      "arrivals_per_s": round(n_arrivals / t_serial_c, 1),
+                                      "loop": "C (xs_serial_replay)"}
+    report["serial_one_at_a_time_python_loop"] = {"gbs": round(total_bytes / t_serial / 1e9, 1),
+                                                  "arrivals_per_s": round(n_arrivals / t_serial, 1)}
+    report["saturated_over_serial"] = round(report["saturated"]["gbs"] / report["serial_one_at_a_time"]["gbs"], 2)
     report["all_results_equal_alone"] = bool(same)
     del arena
     torch.cuda.empty_cache()
@@ -557,24 +578,33 @@ def run_ours(args):
     def step():
         xsum.xs_sum_async(xd, n, out, xsum.XS_METHOD_AUTO, stream)
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize(dev)
-
     # inexact device sums on the same tensor (comparison only)
     t_torch = med_time(torch, stream, lambda: torch.sum(xd))
     t_inexact = med_time(torch, stream, lambda: xsum.xs_inexact_sum_async(xd, n, out, stream))
 
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize(dev)
+    # clocks are sampled from before the warm-up to the end of a sustained block
+    # of steps after the timed region (a window of a second or more, so the
+    # record holds many samples even when the timed region is a few ms)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
         e0.record(stream)
         for _ in range(args.steps):
             step()
         e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sustain_steps = max(args.steps, int(1.5e3 / max(e0.elapsed_time(e1) / args.steps, 1e-3)))
+        s0.record(stream)
+        for _ in range(sustain_steps):
+            step()
+        s1.record(stream)
         torch.cuda.synchronize(dev)
     ms_total = max_over_ranks(torch, e0.elapsed_time(e1), dev)
     ms_step = ms_total / args.steps
@@ -673,6 +703,9 @@ def run_ours(args):
         },
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
+        "sustained_block": {"steps": sustain_steps, "ms_per_step": round(s0.elapsed_time(s1) / sustain_steps, 5),
+                            "note": "after the timed region, same step; the clock record spans warm-up, "
+                                    "timed region and this block"},
         "result_bits": f"{bits_last & ((1 << 64) - 1):#018x}",
     }
     if not args.no_extras:

@@ -165,8 +165,13 @@ xs_status xs_inexact_sum_async(const double* d_values, int64_t n, double* d_out,
 xs_status xs_autotune_sum(const double* d_values, int64_t n, int reps, void* stream,
                           int* best_method, int* best_block, int* best_unroll, float* best_us);
 
-/* Largest n that xs_sum_noalloc accepts: 2^45 terms, the count that the
- * 67-chunk accumulator is guaranteed to hold without overflow. */
+/* Largest n that xs_sum_noalloc accepts: 2^45 terms, a chosen cap (the
+ * headroom the CPU oracle is sized for), far inside what the accumulator
+ * holds. Every per-thread, block and grid chunk bound of the kernel is
+ * independent of n (carries propagate every <= 2047 adds; block partials stay
+ * below 2^41 per chunk), except the top chunk, which carries the sum's high
+ * part: |sum| < n 2^1024 and the top chunk weighs 2^1037, so it stays below
+ * n 2^-13 + 2^32 < 2^63 in magnitude for any n below 2^75. */
 #define XS_NOALLOC_MAX_TERMS (((int64_t)1) << 45)
 
 /* Exact sum for callers that cannot allocate device memory. The paper has no
@@ -204,12 +209,26 @@ xs_status xs_sum_noalloc(const double* d_values, int64_t n, double* d_out, void*
 
 /* d_out[k] = exact sum of d_values[d_offsets[k] .. d_offsets[k+1]) for
  * k < nseg. d_offsets (nseg + 1 int64, device) must start at 0 and never
- * decrease (not checked on the device). One persistent launch behind a CUDA
+ * decrease. The device checks them on every launch: a segment whose start is
+ * negative or whose end lies below its start is not read and gets the default
+ * quiet NaN 0x7FF8000000000000, and the plan records the fault (see
+ * xs_seg_plan_check); offsets past the end of d_values cannot be detected
+ * and must not occur. One persistent launch behind a CUDA
  * graph cached per (values, offsets, nseg, out, stream); asynchronous. The
  * first call for a new key allocates and captures, so make it outside any
  * stream capture. */
 xs_status xs_sum_segments(const double* d_values, const int64_t* d_offsets, int64_t nseg,
                           double* d_out, void* stream);
+
+/* Comparison baseline of the batched form (not a faster path): the same
+ * segment sums as xs_sum_segments, computed as one single-array kernel launch
+ * per segment, issued from a C loop on `stream` in the launch shape
+ * xs_sum_async would choose for each length. Offsets are HOST int64 (nseg + 1,
+ * starting at 0, non-decreasing: checked on the host, XS_ERR_INVALID_VALUE
+ * otherwise); arguments are checked once, not per segment. An empty segment
+ * writes +0.0 with a memset. Asynchronous; same bits as xs_sum_segments. */
+xs_status xs_sum_each_async(const double* d_values, const int64_t* h_offsets, int64_t nseg,
+                            double* d_out, void* stream);
 
 /* Explicit plan: owns the work lists and the instantiated graph. */
 typedef struct xs_seg_plan_s* xs_seg_plan;
@@ -234,6 +253,10 @@ xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const in
 xs_status xs_seg_plan_launch(xs_seg_plan plan, void* stream); /* replays the graph */
 xs_status xs_seg_plan_launch_direct(xs_seg_plan plan, void* stream); /* same kernels, no graph */
 int xs_seg_plan_kernel_launches(xs_seg_plan plan); /* kernels per launch */
+/* Waits for `stream` and reports what the plan's last launch found in the
+ * offsets: XS_ERR_INVALID_VALUE if the first offset was not 0 or some segment
+ * was malformed (those segments hold the default NaN), else XS_OK. */
+xs_status xs_seg_plan_check(xs_seg_plan plan, void* stream);
 xs_status xs_seg_plan_destroy(xs_seg_plan plan);
 
 /* Times candidate xs_seg_options on this input and records the fastest for
@@ -325,6 +348,19 @@ typedef struct xs_replay_item {
  * the last submit; collect results with xs_server_wait. */
 xs_status xs_server_replay(xs_server s, const xs_replay_item* items, int64_t count,
                            uint64_t* request_ids, int64_t* start_ns);
+/* Comparison baseline of the serving loop (not a server): runs the requests of
+ * items[0..count) one at a time in order, each alone, ignoring the arrival
+ * times, from a C loop on `stream`. A one-shot item is one single-array sum
+ * whose result the loop waits for; a session item (same session_tag) is
+ * appended to that session's own device accumulator and waited for, and the
+ * session's finishing item is rounded once (Discussion: partial
+ * superaccumulators add exactly). h_values[k] receives the rounded sum of a
+ * one-shot or finishing item (quiet NaN for appends); done_ns[k] the time, ns
+ * since the call started, at which item k completed. Allocates one 560-byte
+ * accumulator per open session (freed when it finishes or on return). */
+xs_status xs_serial_replay(const xs_replay_item* items, int64_t count, double* h_values,
+                           int64_t* done_ns, void* stream);
+
 /* Waits for every queued and running request, stops the thread, frees. */
 xs_status xs_server_destroy(xs_server s);
 
@@ -348,6 +384,20 @@ xs_status xs_acc_export(xs_acc h, void* h_buf, void* stream); /* XS_ACC_BYTES, b
 xs_status xs_acc_import(xs_acc h, const void* h_buf, void* stream); /* blocking */
 xs_status xs_acc_destroy(xs_acc h);
 void* xs_acc_device_state(xs_acc h); /* device address of the 560-byte state */
+
+/* ---------------------------------------------------------------------------
+ * Test hooks (no counterpart in the paper): allocation-failure injection
+ * ------------------------------------------------------------------------- */
+
+/* Makes the k-th next device or pinned-host allocation of the library (k >= 1;
+ * 1 = the next one) fail as if memory were exhausted, so every entry point's
+ * XS_ERR_OUT_OF_MEMORY path and its unwinding can be tested; k = 0 disarms.
+ * Process-wide; not for production use. */
+xs_status xs_debug_fail_allocation(int64_t k);
+/* Number of device and pinned-host allocations the library currently holds
+ * (workspaces, handles, plans, servers): a failed call must leave it as it
+ * was. */
+int64_t xs_debug_live_allocations(void);
 
 #ifdef __cplusplus
 }

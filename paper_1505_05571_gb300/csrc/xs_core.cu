@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -149,79 +150,104 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
 // Large superaccumulator kernel
 // ---------------------------------------------------------------------------
 
+// One large superaccumulator per block in shared memory (planes of 32-bit
+// words, xs_device.cuh), fed with 32-bit shared atomics; the input streams as
+// in the small kernel (two register buffers used in turn, L2 prefetch). At the
+// end each block transfers its chunks into per-warp small accumulators, adds
+// them into the grid accumulator and the last block rounds.
+// Copies of the lo/hi planes by block size: one block of 512 threads or more
+// per SM holds four, 256-thread blocks (two per SM) two.
+template <int BLOCK>
+constexpr int large_copies() { return BLOCK >= 512 ? 4 : (BLOCK >= 256 ? 2 : 1); }
+template <int BLOCK>
+constexpr size_t large_smem() { return sizeof(LargePlanes<BLOCK / 32, large_copies<BLOCK>()>); }
+
 template <int BLOCK, int UNROLL>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_sum_large(SumArgs a) {
-  static_assert(BLOCK * UNROLL * 2 <= kLCountMax, "a tile must not exceed one chunk's adds");
-  static_assert(UNROLL * 2 <= 32, "failure mask is 32 bits");
+__global__ void __launch_bounds__(BLOCK, (UNROLL >= 8 ? 512 : 768) / BLOCK > 0 ? (UNROLL >= 8 ? 512 : 768) / BLOCK : 1)
+    k_sum_large(SumArgs a) {
+  constexpr int NW = BLOCK / 32;
+  constexpr int R = large_copies<BLOCK>();
   extern __shared__ __align__(16) unsigned char smem_large[];
-  LargeSmem& L = *reinterpret_cast<LargeSmem*>(smem_large);
+  LargePlanes<NW, R>& P = *reinterpret_cast<LargePlanes<NW, R>*>(smem_large);
   const int tid = threadIdx.x;
-  large_init(L, tid, BLOCK);
+  const Split sp = split_input(a.x, a.n);
+  constexpr long long TP = (long long)BLOCK * UNROLL;
+  const long long ntiles = (sp.npairs + TP - 1) / TP;
+  const long long nfull = sp.npairs / TP;
+  const long long G = gridDim.x;
+  long long t = blockIdx.x;
+  if (tid == 0)
+    for (int k = 0; k <= a.prefetch; ++k) prefetch_tile<BLOCK, UNROLL>(sp, t + k * G, ntiles);
+  large_init(P, tid, BLOCK);
+  const LargeLane L = large_lane(P);
   __syncthreads();
   grid_dependency_wait();
-
-  const Split sp = split_input(a.x, a.n);
-  if (blockIdx.x == 0) {  // unaligned head and odd tail, with the special path
+  LargeThread T;
+  ulonglong2 A[UNROLL], B[UNROLL];
+  if (t < nfull) load_full<BLOCK, UNROLL>(sp, t, tid, A);
+  if (blockIdx.x == 0 && tid == 0) {
     const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
-    unsigned long long hb = 0ull, tb = 0ull;
-    bool fh = false, ft = false;
-    if (tid == 0) {
-      if (sp.head) { hb = xb[0]; fh = !large_add(L, hb); }
-      if (sp.tail) { tb = xb[a.n - 1]; ft = !large_add(L, tb); }
+    if (sp.head) {
+      large_one_add(L, xb[0]);
+      T.term(xb[0]);
     }
-    if (__syncthreads_or(fh || ft)) {
-      if (fh) large_fix(L, hb);
-      if (ft) large_fix(L, tb);
-      __syncthreads();
-      if (fh) large_readd(L, hb);
-      if (ft) large_readd(L, tb);
-      __syncthreads();
+    if (sp.tail) {
+      large_one_add(L, xb[a.n - 1]);
+      T.term(xb[a.n - 1]);
     }
   }
-
-  // Several blocks share an SM, so one tile of loads in flight per thread is
-  // enough to cover HBM latency; no register double buffer here.
-  const long long ntiles = (sp.npairs + (long long)(BLOCK * UNROLL) - 1) / (BLOCK * UNROLL);
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    ulonglong2 cur[UNROLL];
-    load_tile<BLOCK, UNROLL>(sp, t, tid, cur);
-    unsigned fail = 0u;
+  while (t < nfull) {
+    if (tid == 0 && a.prefetch > 0) prefetch_tile<BLOCK, UNROLL>(sp, t + (a.prefetch + 1) * G, ntiles);
+    if (t + G < nfull) load_full<BLOCK, UNROLL>(sp, t + G, tid, B);
+    T.group_record<UNROLL>(large_group_add<UNROLL>(L, A), A);
+    t += G;
+    if (t >= nfull) break;
+    if (tid == 0 && a.prefetch > 0) prefetch_tile<BLOCK, UNROLL>(sp, t + (a.prefetch + 1) * G, ntiles);
+    if (t + G < nfull) load_full<BLOCK, UNROLL>(sp, t + G, tid, A);
+    T.group_record<UNROLL>(large_group_add<UNROLL>(L, B), B);
+    t += G;
+  }
+  if (t == nfull && nfull < ntiles) {  // the ragged last tile, term by term
+    const long long base = t * TP + tid;
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
-      if (!large_add(L, cur[u].x)) fail |= 1u << (2 * u);
-      if (!large_add(L, cur[u].y)) fail |= 1u << (2 * u + 1);
+      const long long p = base + (long long)u * BLOCK;
+      if (p < sp.npairs) {
+        const ulonglong2 v = ld_stream(sp.xv + p);
+        large_one_add(L, v.x);
+        large_one_add(L, v.y);
+        T.term(v.x);
+        T.term(v.y);
+      }
     }
-    if (__syncthreads_or(fail != 0u)) {
-#pragma unroll
-      for (int u = 0; u < UNROLL; ++u) {
-        if (fail & (1u << (2 * u))) large_fix(L, cur[u].x);
-        if (fail & (1u << (2 * u + 1))) large_fix(L, cur[u].y);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < UNROLL; ++u) {
-        if (fail & (1u << (2 * u))) large_readd(L, cur[u].x);
-        if (fail & (1u << (2 * u + 1))) large_readd(L, cur[u].y);
-      }
-      __syncthreads();
+  }
+  grid_launch_dependents();
+  // zero/subnormal counts of the block (their spurious implicit bits)
+  {
+    const unsigned zp = __reduce_add_sync(kFull, T.zpos);
+    const unsigned zn = __reduce_add_sync(kFull, T.zneg);
+    if ((tid & 31) == 0) {
+      if (zp) atomicAdd(&P.zeros[0], zp);
+      if (zn) atomicAdd(&P.zeros[1], zn);
     }
   }
   __syncthreads();
-  grid_launch_dependents();
-  large_flush(L, tid, BLOCK);
+  large_flush(P);
   __syncthreads();
   if (tid < kSChunks) {
-    const long long v = L.sacc[tid];
-    if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.g->chunk[tid]),
-                          (unsigned long long)v);
+    long long v = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) v += P.part[w][tid];
+    if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.g->chunk[tid]), (unsigned long long)v);
   }
-  if (tid == 0) {
-    unsigned f = L.flags;
-    if (blockIdx.x == 0 && a.n > 0) f |= kFlagAny;
+  unsigned f = __reduce_or_sync(kFull, T.flags());
+  const unsigned long long key = warp_max_ull(T.nkey);
+  if ((tid & 31) == 0) {
+    if (blockIdx.x == 0 && tid == 0 && a.n > 0) f |= kFlagAny;
     if (f) atomicOr(&a.g->flags, f);
-    if (L.nan_key) atomicMax(&a.g->nan_key, L.nan_key);
+    if (key) atomicMax(&a.g->nan_key, key);
   }
-  finish_grid(a, reinterpret_cast<long long*>(L.chunk));
+  finish_grid(a, reinterpret_cast<long long*>(P.copies));
 }
 
 // ---------------------------------------------------------------------------
@@ -338,9 +364,11 @@ const KernelEntry kKernels[] = {
     {XS_METHOD_SMALL, 384, 4, k_sum_small<384, 4, true>, small_smem<384>()},
     {XS_METHOD_SMALL, 384, 6, k_sum_small<384, 6, false>, small_smem<384>()},
     {XS_METHOD_SMALL, 384, 8, k_sum_small<384, 8, false>, small_smem<384>()},
-    {XS_METHOD_LARGE, 256, 4, k_sum_large<256, 4>, sizeof(LargeSmem)},
-    {XS_METHOD_LARGE, 256, 8, k_sum_large<256, 8>, sizeof(LargeSmem)},
-    {XS_METHOD_LARGE, 128, 8, k_sum_large<128, 8>, sizeof(LargeSmem)},
+    {XS_METHOD_LARGE, 256, 4, k_sum_large<256, 4>, large_smem<256>()},
+    {XS_METHOD_LARGE, 256, 8, k_sum_large<256, 8>, large_smem<256>()},
+    {XS_METHOD_LARGE, 512, 4, k_sum_large<512, 4>, large_smem<512>()},
+    {XS_METHOD_LARGE, 768, 4, k_sum_large<768, 4>, large_smem<768>()},
+    {XS_METHOD_LARGE, 128, 8, k_sum_large<128, 8>, large_smem<128>()},
 };
 constexpr int kNumKernels = sizeof(kKernels) / sizeof(kKernels[0]);
 
@@ -364,6 +392,48 @@ int size_class(int64_t n) {
 }  // namespace
 
 int prefetch_tiles(int builtin) { return g_prefetch_tiles < 0 ? builtin : g_prefetch_tiles; }
+
+
+namespace {
+std::atomic<long long> g_fail_countdown{0};  // k > 0: the k-th next allocation fails
+std::atomic<long long> g_live_allocs{0};
+
+bool injected_failure() {
+  long long k = g_fail_countdown.load();
+  while (k > 0) {
+    if (g_fail_countdown.compare_exchange_weak(k, k - 1)) return k == 1;
+  }
+  return false;
+}
+}  // namespace
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) ++g_live_allocs;
+  return e;
+}
+
+void dev_free(void* p) {
+  if (p == nullptr) return;
+  cudaFree(p);
+  --g_live_allocs;
+}
+
+cudaError_t host_alloc(void** p, size_t bytes, unsigned flags) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaHostAlloc(p, bytes, flags);
+  if (e == cudaSuccess) ++g_live_allocs;
+  return e;
+}
+
+void host_free(void* p) {
+  if (p == nullptr) return;
+  cudaFreeHost(p);
+  --g_live_allocs;
+}
 
 xs_status set_error(xs_status s) {
   g_last = s;
@@ -442,18 +512,19 @@ Workspace* workspace(DeviceCtx* ctx, cudaStream_t s, xs_status* st) {
     return it->second;
   }
   Workspace* w = new Workspace();
-  cudaError_t e = cudaMalloc(&w->acc, 3 * sizeof(AccState) + 64);
+  cudaError_t e = dev_alloc(&w->acc, 3 * sizeof(AccState) + 64);
   if (e == cudaSuccess) e = cudaMemset(w->acc, 0, 3 * sizeof(AccState) + 64);
   if (e == cudaSuccess) {
     w->acc_host = w->acc + 1;
     w->acc_f32 = w->acc + 2;
     w->d_out = reinterpret_cast<double*>(w->acc + 3);
     // mapped: the finishing warp stores the result straight into host memory
-    e = cudaHostAlloc(&w->h_out, sizeof(double), cudaHostAllocMapped);
+    e = host_alloc(&w->h_out, sizeof(double), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&w->h_out_dev), w->h_out, 0);
   }
   if (e != cudaSuccess) {
-    if (w->acc) cudaFree(w->acc);
+    dev_free(w->acc);
+    host_free(w->h_out);
     delete w;
     *st = from_cuda(e);
     return nullptr;
@@ -508,7 +579,7 @@ xs_status launch_small_fixed(const double* d_values, int64_t n, AccState* target
   const long long tile_pairs = (long long)B * U;
   const long long ntiles = std::max<long long>(1, (n / 2 + tile_pairs - 1) / tile_pairs);
   const long long g = std::max<long long>(1, std::min<long long>(grid, ntiles));
-  SumArgs a;
+  SumArgs a{};
   a.x = d_values;
   a.n = n;
   a.g = target;
@@ -676,12 +747,23 @@ xs_status xs_sum_host(const double* h_values, int64_t n, double* h_out, void* st
   if (!w) return st;
   const size_t chunk = size_t(1) << 23;  // 8 Mi doubles (64 MiB) per staging slot
   if (w->stage_elems == 0) {
-    for (int k = 0; k < 2; ++k) {
-      XS_TRY_CUDA(cudaMalloc(&w->stage[k], chunk * sizeof(double)));
-      XS_TRY_CUDA(cudaEventCreateWithFlags(&w->full[k], cudaEventDisableTiming));
-      XS_TRY_CUDA(cudaEventCreateWithFlags(&w->free_[k], cudaEventDisableTiming));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = dev_alloc(&w->stage[k], chunk * sizeof(double));
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->full[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->free_[k], cudaEventDisableTiming);
     }
-    XS_TRY_CUDA(cudaStreamCreateWithFlags(&w->copy_stream, cudaStreamNonBlocking));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {  // leave the workspace as it was: nothing staged
+      for (int k = 0; k < 2; ++k) {
+        dev_free(w->stage[k]);
+        if (w->full[k]) cudaEventDestroy(w->full[k]);
+        if (w->free_[k]) cudaEventDestroy(w->free_[k]);
+        w->stage[k] = nullptr;
+        w->full[k] = w->free_[k] = nullptr;
+      }
+      return from_cuda(e);
+    }
     w->stage_elems = chunk;
   }
   XS_TRY_CUDA(cudaMemsetAsync(w->acc_host, 0, sizeof(AccState), s));
@@ -723,14 +805,18 @@ xs_status xs_inexact_sum_async(const double* d_values, int64_t n, double* d_out,
   if (!ctx) return st;
   Workspace* w = workspace(ctx, s, &st);
   if (!w) return st;
-  static thread_local double* partial = nullptr;
-  static thread_local int partial_dev = -1;
   const int grid = ctx->num_sms * 8;
-  if (partial == nullptr || partial_dev != ctx->device) {
-    XS_TRY_CUDA(cudaMalloc(&partial, (size_t)grid * sizeof(double) + 64));
-    XS_TRY_CUDA(cudaMemset(partial, 0, (size_t)grid * sizeof(double) + 64));
-    partial_dev = ctx->device;
+  if (w->inexact_partial == nullptr) {  // per (device, stream), like the accumulators
+    double* p = nullptr;
+    cudaError_t e = dev_alloc(&p, (size_t)grid * sizeof(double) + 64);
+    if (e == cudaSuccess) e = cudaMemset(p, 0, (size_t)grid * sizeof(double) + 64);
+    if (e != cudaSuccess) {
+      dev_free(p);
+      return from_cuda(e);
+    }
+    w->inexact_partial = p;
   }
+  double* partial = w->inexact_partial;
   unsigned* ticket = reinterpret_cast<unsigned*>(partial + grid);
   k_inexact_sum<<<grid, 256, 0, s>>>(d_values, n, d_out, partial, ticket);
   XS_TRY_CUDA(cudaGetLastError());
@@ -823,7 +909,7 @@ xs_status xs_acc_create(xs_acc* h, void* stream) {
   DeviceCtx* ctx = device_ctx(&st);
   if (!ctx) return st;
   xs_acc a = new xs_acc_s();
-  cudaError_t e = cudaMalloc(&a->d, sizeof(AccState));
+  cudaError_t e = dev_alloc(&a->d, sizeof(AccState));
   if (e != cudaSuccess) {
     delete a;
     return from_cuda(e);
@@ -831,7 +917,7 @@ xs_status xs_acc_create(xs_acc* h, void* stream) {
   a->device = ctx->device;
   e = cudaMemsetAsync(a->d, 0, sizeof(AccState), as_stream(stream));
   if (e != cudaSuccess) {
-    cudaFree(a->d);
+    dev_free(a->d);
     delete a;
     return from_cuda(e);
   }
@@ -910,11 +996,19 @@ xs_status xs_acc_import(xs_acc h, const void* h_buf, void* stream) {
 
 xs_status xs_acc_destroy(xs_acc h) {
   if (h == nullptr) return set_error(XS_ERR_INVALID_POINTER);
-  cudaFree(h->d);
+  dev_free(h->d);
   delete h;
   return set_error(XS_OK);
 }
 
 void* xs_acc_device_state(xs_acc h) { return h ? (void*)h->d : nullptr; }
+
+xs_status xs_debug_fail_allocation(int64_t k) {
+  if (k < 0) return set_error(XS_ERR_INVALID_VALUE);
+  g_fail_countdown.store(k);
+  return set_error(XS_OK);
+}
+
+int64_t xs_debug_live_allocations(void) { return g_live_allocs.load(); }
 
 }  // extern "C"

@@ -6,15 +6,15 @@
 //     2^(32 i - 1075), 32-bit overlap (section "Exact summation using a small
 //     superaccumulator", Fig. 2 and Fig. 3);
 //   * carry propagation at most every 2^11 - 1 adds (same section);
-//   * large superaccumulator: one 64-bit chunk per sign+exponent with a count of
-//     remaining adds, transferred into the small one (section "Faster exact
-//     summation of many terms with a large superaccumulator", Fig. 4);
+//   * large superaccumulator: one chunk per sign+exponent, transferred into
+//     the small one (section "Faster exact summation of many terms with a
+//     large superaccumulator", Fig. 4);
 //   * merge of partial accumulators and one final rounding (Discussion).
 //
 // GPU layout: every thread owns a private small superaccumulator in shared
 // memory, laid out [chunk][thread] so a warp's 64-bit accesses never conflict;
-// a block owns one large superaccumulator in shared memory, updated with shared
-// atomics; block partials meet in one global accumulator through 64-bit integer
+// a block owns one large superaccumulator in shared memory, updated with 32-bit
+// shared atomics; block partials meet in one global accumulator through 64-bit integer
 // atomics (exact and order-free), and the last block to finish rounds.
 #pragma once
 
@@ -27,7 +27,6 @@ constexpr int kSChunks = 67;        // small superaccumulator chunks
 constexpr int kLowExpBits = 5;      // low exponent bits: position inside a chunk
 constexpr int kCarryInterval = 2047;  // adds of <= 2^52-1 between propagations
 constexpr int kLChunks = 4096;      // large superaccumulator: one per sign+exponent
-constexpr int kLCountMax = 4096;    // adds to one large chunk before a transfer
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 constexpr unsigned long long kPosInf = 0x7FF0000000000000ull;
@@ -818,116 +817,226 @@ __device__ __noinline__ static unsigned long long warp_round_div(long long v0, l
 }
 
 // --------------------------------------------------------------------------
-// Large superaccumulator in shared memory, one per block (Fig. 4).
+// Large superaccumulator in shared memory, one per block (Fig. 4), in the
+// form that suits the GPU's shared-memory atomics.
+//
+// As in the paper there is one chunk per sign+exponent index ix = bits >> 52
+// (4096 of them), every term costs one indexed add into its chunk, and the
+// chunks are transferred into the small superaccumulator at the end. What
+// differs: a chunk is a 96-bit unsigned integer held in three planes of 32-bit
+// words (lo, hi, top), and a term adds its 53-bit significand M -- the
+// implicit bit included -- instead of its raw bits. The low word is added with
+// an atomic that returns the old value, so the carry out of it is known and
+// goes into the high word with the rest of M; a carry out of the high word
+// (after at least 2^11 adds to one chunk) adds one to the top word. Nothing
+// ever needs a transfer before the end, so the paper's per-chunk count of the
+// adds left (which bounded a 64-bit chunk to 4096 raw-bit adds) and its
+// special path for the 4096th add are not needed. (A 64-bit shared atomic
+// add costs about three times two 32-bit ones on this GPU, measured.)
+//
+// Terms with e == 0 (zeros and subnormals) also add the implicit bit 2^52;
+// each thread counts them by sign and the flush subtracts the count from
+// chunks 0x000 and 0x800. Inf and NaN terms (e == 2047) land in chunks 0x7FF
+// and 0xFFF, which the flush ignores; their record (Fig. 3's Inf and NaN
+// fields) is kept in registers like the small kernel's.
 // --------------------------------------------------------------------------
 
-struct LargeSmem {
-  unsigned long long chunk[kLChunks];  // raw-bit sums; valid only where used
-  int count[kLChunks];                  // adds left before a transfer; -1 = unused
-  unsigned long long used[kLChunks / 64];  // chunks in use
-  unsigned long long used_used;            // non-empty words of `used`
-  long long sacc[kSChunks];                // transfer target: block small accumulator
-  unsigned flags;
-  unsigned pad;
-  unsigned long long nan_key;
+// Shared-memory layout: R copies of the lo and hi planes (lane L adds into
+// copy L mod R, so R times fewer lanes of a warp meet on one address when few
+// distinct exponents occur; each copy is shifted by 8 banks so the copies of
+// one chunk sit in different banks), one top plane for all copies, and the
+// per-warp transfer targets of the flush. A chunk's value is the sum over the
+// copies of hi:lo, plus top * 2^64.
+template <int NWARPS, int R>
+struct LargePlanes {
+  static constexpr int kCopyWords = 2 * kLChunks + 8;
+  unsigned copies[R * kCopyWords];
+  unsigned top[kLChunks];
+  long long part[NWARPS][kSChunks];
+  unsigned zeros[2];  // zero/subnormal terms of the block, by sign
 };
 
-__device__ __forceinline__ void large_init(LargeSmem& L, int tid, int nthreads) {
-  for (int k = tid; k < kLChunks; k += nthreads) L.count[k] = -1;
-  for (int k = tid; k < kLChunks / 64; k += nthreads) L.used[k] = 0ull;
-  for (int k = tid; k < kSChunks; k += nthreads) L.sacc[k] = 0;
-  if (tid == 0) {
-    L.used_used = 0ull;
-    L.flags = 0u;
-    L.nan_key = 0ull;
+// 32-bit shared-memory atomics on 32-bit shared addresses (volatile: they are
+// neither dropped nor reordered among themselves; the planes are read with
+// plain loads only after a barrier).
+__device__ __forceinline__ unsigned atom_add_shared(unsigned saddr, unsigned v) {
+  unsigned old;
+  asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(saddr), "r"(v));
+  return old;
+}
+__device__ __forceinline__ void red_add_shared(unsigned saddr, unsigned v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(saddr), "r"(v));
+}
+
+// Shared addresses of one lane's view of the planes.
+struct LargeLane {
+  unsigned lo;   // lo plane of the lane's copy (hi follows at + 4 kLChunks bytes)
+  unsigned top;  // the common top plane
+};
+
+// Adds S < 2^64 to chunk ix: the low word with an atomic that returns the old
+// value, the high word with the carry out of it, and a carry out of the high
+// word into the top plane.
+__device__ __forceinline__ void large_add64(const LargeLane& L, unsigned ix, unsigned long long S) {
+  const unsigned l = (unsigned)S;
+  const unsigned old = atom_add_shared(L.lo + (ix << 2), l);
+  unsigned sum, hi;
+  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;"
+      : "=r"(sum), "=r"(hi)
+      : "r"(old), "r"(l), "r"((unsigned)(S >> 32)));
+  const unsigned old2 = atom_add_shared(L.lo + (ix << 2) + 4u * kLChunks, hi);
+  if (old2 + hi < hi) red_add_shared(L.top + (ix << 2), 1u);
+}
+
+// Adds of one group of 2U terms (U 16-byte vectors). The low words of all
+// terms go first, so their atomics' returns are in flight together; then the
+// high words with the carries. When every lane's 2U terms share one index
+// (a constant array, say), each lane adds their sum once instead. Returns the
+// maximum over the terms of ((e - 1) mod 2048) << 20, which reaches
+// 0x7FE00000 exactly when some term has e == 0 or e == 2047 (the rare path).
+template <int U>
+__device__ __forceinline__ unsigned large_group_add(const LargeLane& L, const ulonglong2* v) {
+  unsigned ix[2 * U];
+  unsigned mx = 0u;
+  bool same = true;
+#pragma unroll
+  for (int k = 0; k < 2 * U; ++k) {
+    const unsigned h = (unsigned)(((k & 1) ? v[k >> 1].y : v[k >> 1].x) >> 32);
+    ix[k] = h >> 20;
+    mx = max(mx, (h - 0x00100000u) & 0x7FF00000u);
+    same = same && ix[k] == ix[0];
   }
-}
-
-// Transfer of one large chunk into the block small accumulator (large
-// section): undo the raw sign/exponent bits of the adds not done
-// (index * remaining << 52), add the implicit ones (adds * 2^52) for normal
-// exponents, shift by the low 5 exponent bits and add the three 32-bit pieces
-// to small chunks i, i+1, i+2 with the sign of the index.
-__device__ __forceinline__ void large_transfer(LargeSmem& L, unsigned ix,
-                                               unsigned long long chunkval, int remaining) {
-  const unsigned e = ix & 0x7FFu;
-  const unsigned adds = (unsigned)(kLCountMax - remaining);
-  const unsigned long long sum_m =
-      chunkval + ((unsigned long long)((ix * (unsigned)remaining) & 0xFFFu) << 52);
-  if (adds == 0u) return;
-  if (ix != 0x800u || sum_m != 0ull) atomicOr(&L.flags, kFlagNotNegZero);
-  unsigned __int128 T = sum_m;
-  if (e != 0u) T += ((unsigned __int128)adds) << 52;
-  const unsigned ee = e ? e : 1u;
-  const unsigned i = ee >> kLowExpBits;
-  T <<= (ee & 31u);
-  const long long p0 = (long long)(unsigned)(T);
-  const long long p1 = (long long)(unsigned)(T >> 32);
-  const long long p2 = (long long)(unsigned)(T >> 64);
-  const bool neg = (ix >> 11) != 0u;
-  unsigned long long* s = reinterpret_cast<unsigned long long*>(L.sacc);
-  if (p0) atomicAdd(s + i, (unsigned long long)(neg ? -p0 : p0));
-  if (p1) atomicAdd(s + i + 1, (unsigned long long)(neg ? -p1 : p1));
-  if (p2) atomicAdd(s + i + 2, (unsigned long long)(neg ? -p2 : p2));
-}
-
-// Hot path: count down and add the raw bits (Fig. 4). Returns false when the
-// term needs the special path (first use of the chunk, 4096 adds reached, or
-// Inf/NaN, whose count stays negative).
-__device__ __forceinline__ bool large_add(LargeSmem& L, unsigned long long bits) {
-  const unsigned ix = (unsigned)(bits >> 52);
-  const int old = atomicAdd(&L.count[ix], -1);
-  if (old > 0) {
-    atomicAdd(&L.chunk[ix], bits);
-    return true;
+  if (__all_sync(kFull, same)) {
+    unsigned long long S = 0ull;  // below 2U 2^53
+#pragma unroll
+    for (int k = 0; k < 2 * U; ++k)
+      S += (((k & 1) ? v[k >> 1].y : v[k >> 1].x) & kMantMask) | (1ull << 52);
+    large_add64(L, ix[0], S);
+    return mx;
   }
-  return false;
+  unsigned v2[2 * U];
+#pragma unroll
+  for (int k = 0; k < 2 * U; ++k) {
+    const unsigned long long b = (k & 1) ? v[k >> 1].y : v[k >> 1].x;
+    const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
+    const unsigned old = atom_add_shared(L.lo + (ix[k] << 2), l);
+    unsigned sum, hi;
+    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;"
+        : "=r"(sum), "=r"(hi)
+        : "r"(old), "r"(l), "r"((h & 0xFFFFFu) | 0x100000u));
+    v2[k] = hi;  // (M >> 32) + the carry out of the low word
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * U; ++k) {
+    const unsigned old = atom_add_shared(L.lo + (ix[k] << 2) + 4u * kLChunks, v2[k]);
+    if (old + v2[k] < v2[k]) red_add_shared(L.top + (ix[k] << 2), 1u);
+  }
+  return mx;
 }
 
-// Special path, phase 1 (after a barrier): record Inf/NaN, and for each chunk
-// that refused a term, exactly one thread transfers it (4096 adds done) or
-// marks it used (first use), clears it and resets its count.
-__device__ __forceinline__ void large_fix(LargeSmem& L, unsigned long long bits) {
-  const unsigned ix = (unsigned)(bits >> 52);
-  if ((ix & 0x7FFu) == 0x7FFu) {
-    if (bits & kMantMask) {
-      atomicMax(&L.nan_key, nan_key_of(bits));
+// One term (the unaligned head, the odd tail, the ragged last tile).
+__device__ __forceinline__ void large_one_add(const LargeLane& L, unsigned long long b) {
+  large_add64(L, (unsigned)(b >> 52), (b & kMantMask) | (1ull << 52));
+}
+
+// Per-thread record of the large method: Inf/NaN and the sign of a zero as in
+// SmallThread, plus the zero/subnormal counts by sign.
+struct LargeThread {
+  unsigned notnegz = 0u;
+  unsigned sflags = 0u;
+  unsigned long long nkey = 0ull;
+  unsigned zpos = 0u, zneg = 0u;
+
+  __device__ __forceinline__ void term(unsigned long long b) {
+    const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+    if (e == 0u) {
+      if (b >> 63) ++zneg; else ++zpos;
+      notnegz |= (b != kNegZero) ? 1u : 0u;
+    } else if (e == 0x7FFu) {
+      notnegz = 1u;
+      if (b & kMantMask) {
+        const unsigned long long k = nan_key_of(b);
+        nkey = k > nkey ? k : nkey;
+      } else {
+        sflags |= (b >> 63) ? kFlagNegInf : kFlagPosInf;
+      }
     } else {
-      atomicOr(&L.flags, (ix >> 11) ? kFlagNegInf : kFlagPosInf);
+      notnegz = 1u;
     }
-    atomicOr(&L.flags, kFlagNotNegZero);
-    atomicExch(&L.count[ix], -1);
-    return;
   }
-  const int old = atomicExch(&L.count[ix], kLCountMax);
-  if (old == kLCountMax) return;  // another thread fixed this chunk
-  const unsigned long long ubit = 1ull << (ix & 63u);
-  if (L.used[ix >> 6] & ubit) {
-    large_transfer(L, ix, L.chunk[ix], 0);
-  } else {
-    atomicOr(&L.used[ix >> 6], ubit);
-    atomicOr(&L.used_used, 1ull << (ix >> 6));
+  // after large_group_add: the common case is one compare
+  template <int U>
+  __device__ __forceinline__ void group_record(unsigned mx, const ulonglong2* v) {
+    if (__builtin_expect(mx < 0x7FE00000u, 1)) {
+      notnegz = 1u;
+      return;
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * U; ++k) term((k & 1) ? v[k >> 1].y : v[k >> 1].x);
   }
-  L.chunk[ix] = 0ull;
+  __device__ __forceinline__ unsigned flags() const {
+    return sflags | (notnegz ? kFlagNotNegZero : 0u);
+  }
+};
+
+template <int NWARPS, int R>
+__device__ __forceinline__ void large_init(LargePlanes<NWARPS, R>& P, int tid, int nthreads) {
+  static_assert((R * LargePlanes<NWARPS, R>::kCopyWords + kLChunks) % 4 == 0, "uint4 clear");
+  uint4* w = reinterpret_cast<uint4*>(P.copies);
+  for (int k = tid; k < (R * LargePlanes<NWARPS, R>::kCopyWords + kLChunks) / 4; k += nthreads)
+    w[k] = make_uint4(0u, 0u, 0u, 0u);
+  long long* pp = &P.part[0][0];
+  for (int k = tid; k < NWARPS * kSChunks; k += nthreads) pp[k] = 0;
+  if (tid < 2) P.zeros[tid] = 0u;
 }
 
-// Special path, phase 2 (after another barrier): the refused finite terms are
-// added; their chunks have just been reset, so the count cannot run out.
-__device__ __forceinline__ void large_readd(LargeSmem& L, unsigned long long bits) {
-  const unsigned ix = (unsigned)(bits >> 52);
-  if ((ix & 0x7FFu) == 0x7FFu) return;
-  atomicAdd(&L.count[ix], -1);
-  atomicAdd(&L.chunk[ix], bits);
+template <int NWARPS, int R>
+__device__ __forceinline__ LargeLane large_lane(LargePlanes<NWARPS, R>& P) {
+  const unsigned b = (unsigned)__cvta_generic_to_shared(P.copies);
+  LargeLane L;
+  L.lo = b + 4u * (unsigned)(((threadIdx.x & 31) % R) * LargePlanes<NWARPS, R>::kCopyWords);
+  L.top = (unsigned)__cvta_generic_to_shared(P.top);
+  return L;
 }
 
-// Final transfer of every used chunk (large section: the used flags let the
-// scan skip unused chunks). All threads of the block call it.
-__device__ __forceinline__ void large_flush(LargeSmem& L, int tid, int nthreads) {
-  for (int ix = tid; ix < kLChunks; ix += nthreads) {
-    if (!((L.used_used >> (ix >> 6)) & 1ull)) continue;
-    if (!((L.used[ix >> 6] >> (ix & 63)) & 1ull)) continue;
-    const int rem = L.count[ix];
-    large_transfer(L, (unsigned)ix, L.chunk[ix], rem > 0 ? rem : 0);
+// Final transfer of every chunk into the small superaccumulator (large
+// section; the paper walks the used chunks, here each warp checks 32 chunks at
+// once and skips them when all are zero). Warp w takes the aligned runs of 32
+// indices k = w, w + NWARPS, ...: the 32 chunks of a run share the sign and
+// the small chunk i = max(e, 1) >> 5, so their values (the sum of M over the
+// chunk's terms, shifted left by max(e, 1) & 31: below 2^127) split into four
+// 32-bit pieces for small chunks i..i+3 whose warp sums are formed with 32-bit
+// reductions of 16-bit digits (below 2^21 each, exact) and added, signed, into
+// the warp's own row of `part`. Needs a barrier before (all adds done, zero
+// counts in P.zeros).
+template <int NWARPS, int R>
+__device__ __forceinline__ void large_flush(LargePlanes<NWARPS, R>& P) {
+  constexpr int CW = LargePlanes<NWARPS, R>::kCopyWords;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int run = warp; run < kLChunks / 32; run += NWARPS) {
+    const unsigned ix = (unsigned)run * 32u + (unsigned)lane;
+    const unsigned e = ix & 0x7FFu;
+    unsigned __int128 V = (unsigned __int128)P.top[ix] << 64;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      V += ((unsigned __int128)P.copies[r * CW + kLChunks + ix] << 32) | P.copies[r * CW + ix];
+    if (e == 0x7FFu) V = 0;  // Inf / NaN record only
+    if (e == 0u) V -= (unsigned __int128)P.zeros[ix >> 11] << 52;  // their implicit bits
+    if (!__any_sync(kFull, V != 0)) continue;
+    const unsigned ee = e ? e : 1u;
+    V <<= (ee & 31u);
+    const int i = (int)(ee >> kLowExpBits);  // the same for the whole run
+    const bool neg = (ix >> 11) != 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned p = (unsigned)(V >> (32 * j));
+      const unsigned s0 = __reduce_add_sync(kFull, p & 0xFFFFu);
+      const unsigned s1 = __reduce_add_sync(kFull, p >> 16);
+      if (lane == 0) {
+        const long long S = (long long)s0 + ((long long)s1 << 16);
+        P.part[warp][i + j] += neg ? -S : S;
+      }
+    }
   }
 }
 

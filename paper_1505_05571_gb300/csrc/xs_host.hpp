@@ -23,6 +23,23 @@ xs_status from_cuda(cudaError_t e);  // records and maps a CUDA error
     if (_e != cudaSuccess) return from_cuda(_e); \
   } while (0)
 
+// Every device and pinned-host allocation of the library goes through these
+// four calls. They count the allocations held (xs_debug_live_allocations) and
+// let a test make the k-th next one fail as an out-of-memory error
+// (xs_debug_fail_allocation), so each caller's unwinding can be checked.
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+cudaError_t host_alloc(void** p, size_t bytes, unsigned flags);
+void host_free(void* p);
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc(reinterpret_cast<void**>(p), bytes);
+}
+template <typename T>
+cudaError_t host_alloc(T** p, size_t bytes, unsigned flags) {
+  return host_alloc(reinterpret_cast<void**>(p), bytes, flags);
+}
+
 // Device pointer check (cudaPointerGetAttributes): host or unregistered
 // memory is rejected.
 xs_status check_device_ptr(const void* p);
@@ -42,6 +59,8 @@ struct Workspace {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t full[2] = {nullptr, nullptr};
   cudaEvent_t free_[2] = {nullptr, nullptr};
+  // inexact comparison sum: per-block partials and the ticket behind them
+  double* inexact_partial = nullptr;
 };
 
 struct SumShape {

@@ -37,7 +37,8 @@ struct SegArgs {
   int* slot_of;                // nseg: accumulator slot of a multi-tile segment, else -1
   long long* short_list;       // nseg: indices of short segments
   AccState* slots;             // per multi-tile segment
-  unsigned long long* counters;  // [0] tiles, [1] short segments, [2] tile cursor, [3] short cursor
+  unsigned long long* counters;  // [0] tiles, [1] short segments, [2] tile cursor, [3] short cursor,
+                                 // [4] offsets status of the last launch (kOffBad* bits, 0 = valid)
   long long* blk;               // 3 x nblk: per-block (tiles, short, slots), then their offsets
   long long nblk;               // prep blocks of kPrepSegs segments
   int* tile_seg;                // segment of each tile, when the tiles fit in tile_cap
@@ -81,9 +82,22 @@ __device__ long long block_exclusive_scan(long long v, long long* total, long lo
   return r;
 }
 
+// Offsets status bits (counters[4]): a segment whose start is negative or
+// whose end lies below its start (its values are never read; its result is
+// the default NaN), and a first offset other than 0.
+constexpr unsigned long long kOffBadSegment = 1ull;
+constexpr unsigned long long kOffBadFirst = 2ull;
+
+// A segment is summed only when 0 <= off[s] <= off[s+1]: the sum of a set is
+// defined for a well-formed range only, and a negative start would read
+// before the values.
+__device__ __forceinline__ bool segment_valid(long long start, long long end) {
+  return start >= 0 && end >= start;
+}
+
 // Work lists from the offsets, in three coalesced steps. A prep block owns
 // kPrepSegs consecutive segments, a thread kPrepPer of them; the order of the
-// lists is the order of the segments.
+// lists is the order of the segments. An invalid segment joins no list.
 struct SegCounts {
   long long tiles, shorts, slots;
 };
@@ -91,6 +105,7 @@ __device__ __forceinline__ SegCounts thread_counts(const SegArgs& a, long long s
   SegCounts c{0, 0, 0};
   for (long long s = s0; s < s1; ++s) {
     const long long L = a.off[s + 1] - a.off[s];
+    if (!segment_valid(a.off[s], a.off[s + 1])) continue;
     if (L > a.short_max) {
       const long long t = (L + a.tile_elems - 1) / a.tile_elems;
       c.tiles += t;
@@ -141,6 +156,7 @@ __global__ void __launch_bounds__(1024) k_seg_scan(SegArgs a) {
   if (threadIdx.x == 0) {
     a.counters[2] = 0ull;
     a.counters[3] = 0ull;
+    a.counters[4] = 0ull;  // k_seg_fill records what it finds
   }
 }
 
@@ -153,11 +169,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_seg_fill(SegArgs a) {
   long long t_off = a.blk[blockIdx.x] + block_exclusive_scan(c.tiles, &tot, sbuf);
   long long sh_off = a.blk[a.nblk + blockIdx.x] + block_exclusive_scan(c.shorts, &tot, sbuf);
   long long sl_off = a.blk[2 * a.nblk + blockIdx.x] + block_exclusive_scan(c.slots, &tot, sbuf);
+  unsigned long long bad = (blockIdx.x == 0 && threadIdx.x == 0 && a.off[0] != 0) ? kOffBadFirst : 0ull;
   for (long long s = s0; s < s1; ++s) {
     const long long L = a.off[s + 1] - a.off[s];
     a.tile_start[s] = t_off;
     int slot = -1;
-    if (L > a.short_max) {
+    if (!segment_valid(a.off[s], a.off[s + 1])) {
+      reinterpret_cast<unsigned long long*>(a.out)[s] = kDefaultNaN;
+      bad |= kOffBadSegment;
+    } else if (L > a.short_max) {
       const long long t = (L + a.tile_elems - 1) / a.tile_elems;
       if (t_off + t <= a.tile_cap)
         for (long long k = 0; k < t; ++k) a.tile_seg[t_off + k] = (int)s;
@@ -168,6 +188,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_seg_fill(SegArgs a) {
     }
     a.slot_of[s] = slot;
   }
+  if (bad) atomicOr(&a.counters[4], bad);
 }
 
 constexpr int kPhase1Ahead = 48;  // values per thread of a tile prefetched before the block starts it
@@ -670,7 +691,7 @@ xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const in
   const size_t tile_cap = n + (size_t)(last / o.tile_elems) + 1;
   const size_t bytes_tab = ((tile_cap * sizeof(int) + 15) / 16) * 16;
   const size_t total = bytes_ctr + bytes_ts + bytes_sl + bytes_so + bytes_slots + bytes_blk + bytes_tab;
-  cudaError_t e = cudaMalloc(&p->mem, total);
+  cudaError_t e = dev_alloc(&p->mem, total);
   if (e != cudaSuccess) {
     delete p;
     return from_cuda(e);
@@ -678,7 +699,7 @@ xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const in
   cudaStream_t s = as_stream(stream);
   e = cudaMemsetAsync(p->mem, 0, total, s);
   if (e != cudaSuccess) {
-    cudaFree(p->mem);
+    dev_free(p->mem);
     delete p;
     return from_cuda(e);
   }
@@ -715,7 +736,7 @@ xs_status xs_seg_plan_create(xs_seg_plan* plan, const double* d_values, const in
   cudaStreamDestroy(cs);
   if (e != cudaSuccess) {
     if (p->graph) cudaGraphDestroy(p->graph);
-    cudaFree(p->mem);
+    dev_free(p->mem);
     delete p;
     return from_cuda(e);
   }
@@ -738,11 +759,20 @@ xs_status xs_seg_plan_launch_direct(xs_seg_plan p, void* stream) {
 
 int xs_seg_plan_kernel_launches(xs_seg_plan p) { return p ? 4 : 0; }
 
+xs_status xs_seg_plan_check(xs_seg_plan p, void* stream) {
+  if (p == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  unsigned long long bad = 0ull;
+  cudaStream_t s = as_stream(stream);
+  XS_TRY_CUDA(cudaMemcpyAsync(&bad, &p->args.counters[4], sizeof bad, cudaMemcpyDeviceToHost, s));
+  XS_TRY_CUDA(cudaStreamSynchronize(s));
+  return set_error(bad ? XS_ERR_INVALID_VALUE : XS_OK);
+}
+
 xs_status xs_seg_plan_destroy(xs_seg_plan p) {
   if (p == nullptr) return set_error(XS_ERR_INVALID_POINTER);
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
-  cudaFree(p->mem);
+  dev_free(p->mem);
   delete p;
   return set_error(XS_OK);
 }
@@ -755,6 +785,38 @@ std::map<std::tuple<int, const void*, const void*, int64_t, void*, void*>, xs_se
 }  // namespace
 
 extern "C" {
+
+xs_status xs_sum_each_async(const double* d_values, const int64_t* h_offsets, int64_t nseg,
+                            double* d_out, void* stream) {
+  if (nseg < 0) return set_error(XS_ERR_INVALID_VALUE);
+  if (nseg == 0) return set_error(XS_OK);
+  if (h_offsets == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  if (h_offsets[0] != 0) return set_error(XS_ERR_INVALID_VALUE);
+  for (int64_t k = 0; k < nseg; ++k)
+    if (h_offsets[k + 1] < h_offsets[k]) return set_error(XS_ERR_INVALID_VALUE);
+  xs_status st;
+  if ((st = check_device_ptr(d_out)) != XS_OK) return st;
+  if (h_offsets[nseg] > 0 && (st = check_device_ptr(d_values)) != XS_OK) return st;
+  if (((uintptr_t)d_values & 7u) || ((uintptr_t)d_out & 7u)) return set_error(XS_ERR_INVALID_VALUE);
+  cudaStream_t s = as_stream(stream);
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  Workspace* w = workspace(ctx, s, &st);
+  if (!w) return st;
+  // arguments are checked once above; each segment is then one launch of the
+  // single-array kernel in the shape xs_sum_async would choose for its length
+  for (int64_t k = 0; k < nseg; ++k) {
+    const int64_t len = h_offsets[k + 1] - h_offsets[k];
+    if (len == 0) {
+      XS_TRY_CUDA(cudaMemsetAsync(d_out + k, 0, sizeof(double), s));
+      continue;
+    }
+    st = launch_sum(ctx, d_values + h_offsets[k], len, w->acc, d_out + k, 0, default_shape(ctx, len),
+                    0, s);
+    if (st != XS_OK) return st;
+  }
+  return set_error(XS_OK);
+}
 
 xs_status xs_sum_segments(const double* d_values, const int64_t* d_offsets, int64_t nseg,
                           double* d_out, void* stream) {

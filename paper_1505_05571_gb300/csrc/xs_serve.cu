@@ -230,6 +230,18 @@ __global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
   }
 }
 
+// Rounded value of a session accumulator (normalised, state left unchanged),
+// for the serial baseline. One warp.
+__global__ void k_serial_round(const AccState* acc, double* out) {
+  __shared__ long long sc[kSChunks];
+  const int lane = threadIdx.x;
+  const long long v0 = acc->chunk[lane];
+  const long long v1 = acc->chunk[lane + 32];
+  const long long v2 = lane < 3 ? acc->chunk[lane + 64] : 0;
+  const unsigned long long bits = warp_round(v0, v1, v2, acc->flags, acc->nan_key, sc, 32);
+  if (lane == 0) *reinterpret_cast<unsigned long long*>(out) = bits;
+}
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -507,10 +519,10 @@ xs_status xs_server_create(xs_server* out, const xs_server_options* opts) {
     for (BatchSlot& b : s->batches) {
       if (b.stream) cudaStreamDestroy(b.stream);
       if (b.done) cudaEventDestroy(b.done);
-      if (b.d_mem) cudaFree(b.d_mem);
-      if (b.h_mem) cudaFreeHost(b.h_mem);
+      dev_free(b.d_mem);
+      host_free(b.h_mem);
     }
-    if (s->d_slots) cudaFree(s->d_slots);
+    dev_free(s->d_slots);
     delete s;
     return from_cuda(e);
   };
@@ -523,7 +535,7 @@ xs_status xs_server_create(xs_server* out, const xs_server_options* opts) {
                                                       kServeBlock, smem);
   if (e != cudaSuccess) return fail(e);
   s->grid = ctx->num_sms * std::max(1, occ);
-  e = cudaMalloc(&s->d_slots, (size_t)o.max_sessions * sizeof(AccState));
+  e = dev_alloc(&s->d_slots, (size_t)o.max_sessions * sizeof(AccState));
   if (e == cudaSuccess) e = cudaMemset(s->d_slots, 0, (size_t)o.max_sessions * sizeof(AccState));
   if (e != cudaSuccess) return fail(e);
   for (int k = o.max_sessions - 1; k >= 0; --k) s->free_slots.push_back(k);
@@ -534,8 +546,8 @@ xs_status xs_server_create(xs_server* out, const xs_server_options* opts) {
   for (BatchSlot& b : s->batches) {
     e = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&b.d_mem, total);
-    if (e == cudaSuccess) e = cudaMallocHost(&b.h_mem, total);
+    if (e == cudaSuccess) e = dev_alloc(&b.d_mem, total);
+    if (e == cudaSuccess) e = host_alloc(&b.h_mem, total, cudaHostAllocDefault);
     if (e != cudaSuccess) return fail(e);
     char* d = static_cast<char*>(b.d_mem);
     char* h = static_cast<char*>(b.h_mem);
@@ -695,6 +707,82 @@ xs_status xs_server_replay(xs_server s, const xs_replay_item* items, int64_t cou
   return set_error(XS_OK);
 }
 
+xs_status xs_serial_replay(const xs_replay_item* items, int64_t count, double* h_values,
+                           int64_t* done_ns, void* stream) {
+  if (count < 0) return set_error(XS_ERR_INVALID_VALUE);
+  if (count > 0 && (items == nullptr || h_values == nullptr || done_ns == nullptr))
+    return set_error(XS_ERR_INVALID_POINTER);
+  xs_status st;
+  cudaStream_t s = as_stream(stream);
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  Workspace* w = workspace(ctx, s, &st);
+  if (!w) return st;
+  std::unordered_map<uint64_t, AccState*> open;  // session tag -> its accumulator
+  auto release = [&]() {
+    for (auto& kv : open) dev_free(kv.second);
+    open.clear();
+  };
+  const Clock::time_point t0 = Clock::now();
+  unsigned long long nan_bits = 0x7FF8000000000000ull;
+  for (int64_t k = 0; k < count; ++k) {
+    const xs_replay_item& it = items[k];
+    std::memcpy(&h_values[k], &nan_bits, sizeof(double));
+    if (it.n < 0) {
+      release();
+      return set_error(XS_ERR_INVALID_VALUE);
+    }
+    if (it.session_tag == 0) {  // a one-shot sum: one kernel, then wait for its result
+      st = xs_sum_ex(it.d_values, it.n, stream, &h_values[k]);
+      if (st != XS_OK) {
+        release();
+        return st;
+      }
+    } else {
+      auto o = open.find(it.session_tag);
+      if (o == open.end()) {
+        AccState* a = nullptr;
+        cudaError_t e = dev_alloc(&a, sizeof(AccState));
+        if (e == cudaSuccess) e = cudaMemsetAsync(a, 0, sizeof(AccState), s);
+        if (e != cudaSuccess) {
+          dev_free(a);
+          release();
+          return from_cuda(e);
+        }
+        o = open.emplace(it.session_tag, a).first;
+      }
+      if (it.n > 0) {
+        st = launch_sum(ctx, it.d_values, it.n, o->second, nullptr, 1, default_shape(ctx, it.n), 0, s);
+        if (st != XS_OK) {
+          release();
+          return st;
+        }
+      }
+      if (it.flags & XS_REQ_FINISH) {
+        k_serial_round<<<1, 32, 0, s>>>(o->second, w->h_out_dev);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+          release();
+          return from_cuda(e);
+        }
+        h_values[k] = *static_cast<volatile double*>(w->h_out);
+        dev_free(o->second);
+        open.erase(o);
+      } else {
+        const cudaError_t e = cudaStreamSynchronize(s);  // one request at a time
+        if (e != cudaSuccess) {
+          release();
+          return from_cuda(e);
+        }
+      }
+    }
+    done_ns[k] = std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t0).count();
+  }
+  release();
+  return set_error(XS_OK);
+}
+
 xs_status xs_server_destroy(xs_server s) {
   if (s == nullptr) return set_error(XS_ERR_INVALID_POINTER);
   {
@@ -707,10 +795,10 @@ xs_status xs_server_destroy(xs_server s) {
     cudaStreamSynchronize(b.stream);
     cudaStreamDestroy(b.stream);
     cudaEventDestroy(b.done);
-    cudaFree(b.d_mem);
-    cudaFreeHost(b.h_mem);
+    dev_free(b.d_mem);
+    host_free(b.h_mem);
   }
-  cudaFree(s->d_slots);
+  dev_free(s->d_slots);
   for (auto& kv : s->reqs) delete kv.second;
   delete s;
   return set_error(XS_OK);

@@ -102,11 +102,13 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "xs_sum_segments": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, _vp]),
+    "xs_sum_each_async": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, _vp]),
     "xs_seg_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, _vp, _c_int64, _vp,
                                           ctypes.POINTER(xs_seg_options), _vp]),
     "xs_seg_plan_launch": (ctypes.c_int, [_vp, _vp]),
     "xs_seg_plan_launch_direct": (ctypes.c_int, [_vp, _vp]),
     "xs_seg_plan_kernel_launches": (ctypes.c_int, [_vp]),
+    "xs_seg_plan_check": (ctypes.c_int, [_vp, _vp]),
     "xs_seg_plan_destroy": (ctypes.c_int, [_vp]),
     "xs_autotune_segments": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, ctypes.c_int, _vp,
                                             ctypes.POINTER(xs_seg_options),
@@ -120,6 +122,9 @@ _SIGS = {
     "xs_server_destroy": (ctypes.c_int, [_vp]),
     "xs_server_replay": (ctypes.c_int, [_vp, ctypes.POINTER(xs_replay_item), ctypes.c_int64,
                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int64)]),
+    "xs_serial_replay": (ctypes.c_int, [ctypes.POINTER(xs_replay_item), ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                        _vp]),
     "xs_acc_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp]),
     "xs_acc_init": (ctypes.c_int, [_vp, _vp]),
     "xs_acc_add": (ctypes.c_int, [_vp, _vp, _c_int64, _vp]),
@@ -129,6 +134,8 @@ _SIGS = {
     "xs_acc_import": (ctypes.c_int, [_vp, _vp, _vp]),
     "xs_acc_destroy": (ctypes.c_int, [_vp]),
     "xs_acc_device_state": (_vp, [_vp]),
+    "xs_debug_fail_allocation": (ctypes.c_int, [_c_int64]),
+    "xs_debug_live_allocations": (_c_int64, []),
 }
 
 _lib = None
@@ -303,6 +310,14 @@ def xs_sum_segments(d_values, d_offsets, nseg: int, d_out, stream=None) -> None:
                                   _stream(stream)), "xs_sum_segments")
 
 
+def xs_sum_each_async(d_values, h_offsets, nseg: int, d_out, stream=None) -> None:
+    """h_offsets: a host int64 buffer (numpy array, or an address)."""
+    if hasattr(h_offsets, "ctypes"):
+        h_offsets = h_offsets.ctypes.data
+    _check(load().xs_sum_each_async(_ptr(d_values), _ptr(h_offsets), nseg, _ptr(d_out),
+                                    _stream(stream)), "xs_sum_each_async")
+
+
 def _opts(opts) -> xs_seg_options | None:
     if opts is None:
         return None
@@ -333,6 +348,11 @@ def xs_seg_plan_launch_direct(plan: int, stream=None) -> None:
 
 def xs_seg_plan_kernel_launches(plan: int) -> int:
     return load().xs_seg_plan_kernel_launches(plan)
+
+
+def xs_seg_plan_check(plan: int, stream=None) -> None:
+    """Raises XsError(XS_ERR_INVALID_VALUE) if the last launch found malformed offsets."""
+    _check(load().xs_seg_plan_check(plan, _stream(stream)), "xs_seg_plan_check")
 
 
 def xs_seg_plan_destroy(plan: int) -> None:
@@ -391,6 +411,14 @@ def xs_acc_device_state(h: int) -> int:
     return load().xs_acc_device_state(h)
 
 
+def xs_debug_fail_allocation(k: int) -> None:
+    _check(load().xs_debug_fail_allocation(k), "xs_debug_fail_allocation")
+
+
+def xs_debug_live_allocations() -> int:
+    return load().xs_debug_live_allocations()
+
+
 def acc_state_chunks(state: bytes) -> list[int]:
     """The 67 signed chunks of an exported state (little-endian int64)."""
     return list(struct.unpack("<67q", state[:536]))
@@ -446,11 +474,25 @@ def xs_server_destroy(server: int) -> None:
 
 def xs_server_replay(server: int, items) -> tuple[list[int], int]:
     """items: sequence of (t_ns, session_tag, d_values_ptr, n, flags). Returns (ids, start_ns)."""
-    arr = (xs_replay_item * len(items))()
-    for k, (t, tag, ptr, n, fl) in enumerate(items):
-        arr[k] = xs_replay_item(int(t), int(tag), int(ptr), int(n), int(fl), 0)
+    arr = _replay_items(items)
     ids = (ctypes.c_uint64 * len(items))()
     start = ctypes.c_int64()
     _check(load().xs_server_replay(server, arr, len(items), ids, ctypes.byref(start)),
            "xs_server_replay")
     return list(ids), start.value
+
+
+def _replay_items(items):
+    arr = (xs_replay_item * len(items))()
+    for k, (t, tag, ptr, n, fl) in enumerate(items):
+        arr[k] = xs_replay_item(int(t), int(tag), int(ptr), int(n), int(fl), 0)
+    return arr
+
+
+def xs_serial_replay(items, stream=None) -> tuple[list[float], list[int]]:
+    """items as for xs_server_replay. Returns (values, done_ns) per item."""
+    arr = _replay_items(items)
+    vals = (ctypes.c_double * len(items))()
+    done = (ctypes.c_int64 * len(items))()
+    _check(load().xs_serial_replay(arr, len(items), vals, done, _stream(stream)), "xs_serial_replay")
+    return list(vals), list(done)

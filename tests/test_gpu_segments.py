@@ -8,7 +8,7 @@ import workloads as W
 from oracle import c_oracle
 from paper_1505_05571_gb300 import xsum
 from tests.gpu_util import bits_of, to_device
-from workloads import devgen
+from workloads import devgen, hostgen
 
 pytestmark = pytest.mark.gpu
 
@@ -119,9 +119,29 @@ def test_segments_autotune_then_default():
     assert np.array_equal(got, c_oracle.segment_sums_bits(vals, off))
 
 
-def test_full_cfg3_sampled():
-    """100,000 segments, lengths log-uniform in [1, 1e6] (about 7.2e9 values,
-    58 GB generated in HBM); sampled segments checked against the oracle."""
+def cfg3_oracle_all(off: np.ndarray, seed: int = 0, slice_values: int = 1 << 28) -> np.ndarray:
+    """Oracle bits of every segment of the segmented workload: the host
+    regenerates the values in slices of whole segments (about 2 GB each, on
+    every host core) and the C oracle sums each slice's segments on OpenMP
+    threads."""
+    nseg = off.size - 1
+    expect = np.empty(nseg, dtype=np.uint64)
+    buf = np.empty(max(slice_values, int(np.diff(off).max())), dtype=np.uint64)
+    s0 = 0
+    while s0 < nseg:
+        s1 = int(np.searchsorted(off, off[s0] + slice_values, side="right")) - 1
+        s1 = min(max(s1, s0 + 1), nseg)
+        lo, hi = int(off[s0]), int(off[s1])
+        vals = hostgen.band(seed, lo, hi - lo, -30, 30, out=buf)
+        expect[s0:s1] = c_oracle.segment_sums_bits(vals, off[s0:s1 + 1] - lo)
+        s0 = s1
+    return expect
+
+
+def test_full_cfg3_every_segment():
+    """100,000 segments, lengths log-uniform in [1, 1e6] (about 7.3e9 values,
+    58 GB generated in HBM), autotuned options: every segment's sum equals the
+    oracle's bit for bit."""
     nseg = 100_000
     lengths = W.cfg3_lengths(0, nseg, 10 ** 6)
     off = W.cfg3_offsets(lengths)
@@ -133,16 +153,25 @@ def test_full_cfg3_sampled():
     devgen.band(vals, 0, 0, -30, 30)
     od = torch.from_numpy(off).cuda()
     out = torch.empty(nseg, dtype=torch.float64, device="cuda")
-    xsum.xs_sum_segments(vals.view(torch.float64), od, nseg, out)
-    got = bits_of(out)
-    del vals
+    vd = vals.view(torch.float64)
+    got = {}
+    xsum.xs_sum_segments(vd, od, nseg, out)  # default options
+    got["default"] = bits_of(out)
+    xsum.xs_autotune_segments(vd, od, nseg, out, reps=1)
+    out.fill_(float("nan"))
+    p = xsum.xs_seg_plan_create(vd, od, nseg, out, None)  # the tuned options
+    try:
+        xsum.xs_seg_plan_launch(p)
+        torch.cuda.synchronize()
+    finally:
+        xsum.xs_seg_plan_destroy(p)
+    got["tuned"] = bits_of(out)
+    del vals, vd
     torch.cuda.empty_cache()
-    rng = np.random.default_rng(0)
-    sample = np.unique(np.concatenate([rng.integers(0, nseg, 120), np.argsort(lengths)[-8:],
-                                       np.argsort(lengths)[:8]]))
-    for s in sample:
-        seg = W.cfg3_values(0, int(off[s]), int(lengths[s]))
-        assert got[s] == c_oracle.sum_bits(seg), int(s)
+    expect = cfg3_oracle_all(off)
+    for name, g in got.items():
+        bad = np.nonzero(g != expect)[0]
+        assert bad.size == 0, (name, bad.size, [(int(k), int(lengths[k])) for k in bad[:5]])
 
 
 @pytest.mark.parametrize("tile", [1 << 20, 1 << 22, 3_000_001])
@@ -236,3 +265,66 @@ def test_offsets_rewritten_in_place_past_the_tile_table(block, unroll):
         assert np.array_equal(bits_of(out), c_oracle.segment_sums_bits(vals, off_big))
     finally:
         xsum.xs_seg_plan_destroy(p)
+
+
+def test_one_launch_per_segment_baseline_matches_oracle():
+    """The comparison baseline (one single-array launch per segment from a C
+    loop, host offsets) gives the oracle's bits, empty segments included."""
+    nseg = 700
+    lengths = mixed_lengths(5, nseg)
+    off = W.cfg3_offsets(lengths)
+    vals = W.cfg3_values(5, 0, int(off[-1]))
+    vd = to_device(vals, misalign=1)
+    out = torch.full((nseg,), float("nan"), dtype=torch.float64, device="cuda")
+    xsum.xs_sum_each_async(vd, off, nseg, out)
+    assert np.array_equal(bits_of(out), c_oracle.segment_sums_bits(vals, off))
+    bad = off.copy()
+    bad[3], bad[4] = bad[4], bad[3]  # decreasing offsets: rejected on the host
+    if bad[3] != bad[4]:
+        with pytest.raises(xsum.XsError) as e:
+            xsum.xs_sum_each_async(vd, bad, nseg, out)
+        assert e.value.status == xsum.XS_ERR_INVALID_VALUE
+
+
+def test_malformed_offsets_are_flagged_and_not_read():
+    """Offsets that decrease (all inside the values, so nothing out of bounds
+    is ever at stake) and a first offset other than 0: the launch flags the
+    plan, each malformed segment holds the default NaN without being read,
+    and every well-formed segment is still the oracle's sum."""
+    vals = W.cfg3_values(8, 0, 100_000)
+    vd = to_device(vals)
+    cases = [
+        np.array([0, 10, 5, 20_000, 20_000, 90_000, 30, 40], dtype=np.int64),  # two decreases
+        np.array([7, 500, 70_000, 99_000], dtype=np.int64),                      # first offset not 0
+        np.array([0, 60_000, 100_000], dtype=np.int64),                          # well formed
+    ]
+    for off in cases:
+        nseg = off.size - 1
+        od = torch.from_numpy(off).cuda()
+        for opts in (None, {"block": 128, "unroll": 8, "tile_elems": 4096, "short_max": 64}):
+            out = torch.zeros(nseg, dtype=torch.float64, device="cuda")
+            p = xsum.xs_seg_plan_create(vd, od, nseg, out, opts)
+            try:
+                xsum.xs_seg_plan_launch(p)
+                bad = [k for k in range(nseg) if off[k + 1] < off[k] or off[k] < 0]
+                if bad or off[0] != 0:
+                    with pytest.raises(xsum.XsError) as e:
+                        xsum.xs_seg_plan_check(p)
+                    assert e.value.status == xsum.XS_ERR_INVALID_VALUE
+                else:
+                    xsum.xs_seg_plan_check(p)
+                got = bits_of(out)
+                for k in range(nseg):
+                    if k in bad:
+                        assert got[k] == 0x7FF8000000000000, k
+                    else:
+                        assert got[k] == c_oracle.sum_bits(vals[off[k]:off[k + 1]]), k
+                # the status is per launch: after the offsets are fixed in place it clears
+                if bad:
+                    good = np.maximum.accumulate(off) - off[0]
+                    od.copy_(torch.from_numpy(good))
+                    xsum.xs_seg_plan_launch(p)
+                    xsum.xs_seg_plan_check(p)
+                    od.copy_(torch.from_numpy(off))
+            finally:
+                xsum.xs_seg_plan_destroy(p)

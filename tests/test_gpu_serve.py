@@ -187,3 +187,29 @@ def test_tile_size_limits():
         with pytest.raises(xsum.XsError) as e:
             xsum.xs_server_create(tile_elems=bad)
         assert e.value.status == xsum.XS_ERR_INVALID_VALUE
+
+
+def test_serial_replay_matches_oracle():
+    """The serial baseline (one request at a time, from a C loop): one-shot sums
+    and sessions interleaved in the trace, each result the oracle's bits."""
+    x, d = make_pool()
+    base = d.data_ptr()
+    rng = np.random.default_rng(11)
+    items, expect = [], {}
+    for k in range(40):
+        if rng.random() < 0.5:
+            lo, hi = random_range(rng, x.size)
+            items.append((0, 0, base + 8 * lo, hi - lo, 0))
+            expect[len(items) - 1] = c_oracle.sum_bits(x[lo:hi])
+        else:
+            ranges = [random_range(rng, x.size) for _ in range(int(rng.geometric(0.3)))]
+            for j, (lo, hi) in enumerate(ranges):
+                fin = j == len(ranges) - 1
+                items.append((0, k + 1, base + 8 * lo, hi - lo, xsum.XS_REQ_FINISH if fin else 0))
+            expect[len(items) - 1] = c_oracle.sum_bits(np.concatenate([x[lo:hi] for lo, hi in ranges]))
+    items.append((0, 0, base, 0, 0))  # an empty one-shot sum
+    expect[len(items) - 1] = 0
+    vals, done = xsum.xs_serial_replay(items)
+    assert all(b >= a for a, b in zip(done, done[1:]))
+    for k, e in expect.items():
+        assert f2b(vals[k]) == e, k
