@@ -307,10 +307,34 @@ def extra_configs(torch, np, xsum, devgen, W, dev, stream, rate_gbs, xd, n):
     bits = lambda t: int(t.view(torch.int64).item()) & ((1 << 64) - 1)  # noqa: E731
     res = torch.empty(1, dtype=torch.float64, device=dev)
 
-    # the paper's large superaccumulator method on the same array
-    t_large = med_time(torch, stream, lambda: xsum.xs_sum_async(xd, n, res, xsum.XS_METHOD_LARGE, stream))
-    out["large_method_cfg1"] = {"us": round(t_large * 1000, 2),
-                                "gbs": round(8 * n / (t_large * 1e-3) / 1e9, 1)}
+    # both methods on the same array, and on other value distributions of the
+    # same size (per call, back to back): the large superaccumulator is the
+    # default at this size; the small one is the other choice
+    per_method = {}
+    for name, m in (("small", xsum.XS_METHOD_SMALL), ("large", xsum.XS_METHOD_LARGE)):
+        t = b2b_time(torch, stream, lambda: xsum.xs_sum_async(xd, n, res, m, stream))
+        per_method[name] = {"us": round(t * 1000, 2), "gbs": round(8 * n / (t * 1e-3) / 1e9, 1)}
+    out["methods_cfg1"] = per_method
+    other = torch.empty(n, dtype=torch.float64, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    dists = {}
+    for name in ("uniform(-1,1)", "normal(0,1)", "uniform(1,2) either sign", "constant 0.1"):
+        if name == "uniform(-1,1)":
+            other.uniform_(-1.0, 1.0, generator=g)
+        elif name == "normal(0,1)":
+            other.normal_(generator=g)
+        elif name == "uniform(1,2) either sign":
+            other.uniform_(1.0, 2.0, generator=g)
+            other.mul_(torch.randint(0, 2, (n,), device=dev, generator=g).to(torch.float64) * 2 - 1)
+        else:
+            other.fill_(0.1)
+        row = {}
+        for mname, m in (("small_us", xsum.XS_METHOD_SMALL), ("large_us", xsum.XS_METHOD_LARGE)):
+            row[mname] = round(b2b_time(torch, stream, lambda: xsum.xs_sum_async(other, n, res, m, stream)) * 1000, 1)
+        dists[name] = row
+    out["methods_by_distribution_1e8"] = dists
+    del other
 
     # cfg0: n = 10,000 with heavy cancellation -- latency
     x0 = torch.from_numpy(W.cfg0_cancel(0)).to(dev)

@@ -162,9 +162,12 @@ constexpr int large_copies() { return BLOCK >= 512 ? 4 : (BLOCK >= 256 ? 2 : 1);
 template <int BLOCK>
 constexpr size_t large_smem() { return sizeof(LargePlanes<BLOCK / 32, large_copies<BLOCK>()>); }
 
+// Blocks per SM that the shared memory allows (227 KB): 4, 2, 1.
+template <int BLOCK>
+constexpr int large_blocks_per_sm() { return BLOCK >= 512 ? 1 : (BLOCK >= 256 ? 2 : 4); }
+
 template <int BLOCK, int UNROLL>
-__global__ void __launch_bounds__(BLOCK, (UNROLL >= 8 ? 512 : 768) / BLOCK > 0 ? (UNROLL >= 8 ? 512 : 768) / BLOCK : 1)
-    k_sum_large(SumArgs a) {
+__global__ void __launch_bounds__(BLOCK, large_blocks_per_sm<BLOCK>()) k_sum_large(SumArgs a) {
   constexpr int NW = BLOCK / 32;
   constexpr int R = large_copies<BLOCK>();
   extern __shared__ __align__(16) unsigned char smem_large[];
@@ -367,6 +370,7 @@ const KernelEntry kKernels[] = {
     {XS_METHOD_LARGE, 256, 4, k_sum_large<256, 4>, large_smem<256>()},
     {XS_METHOD_LARGE, 256, 8, k_sum_large<256, 8>, large_smem<256>()},
     {XS_METHOD_LARGE, 512, 4, k_sum_large<512, 4>, large_smem<512>()},
+    {XS_METHOD_LARGE, 512, 8, k_sum_large<512, 8>, large_smem<512>()},
     {XS_METHOD_LARGE, 768, 4, k_sum_large<768, 4>, large_smem<768>()},
     {XS_METHOD_LARGE, 128, 8, k_sum_large<128, 8>, large_smem<128>()},
 };
@@ -537,10 +541,25 @@ Workspace* workspace(DeviceCtx* ctx, cudaStream_t s, xs_status* st) {
 SumShape default_shape(DeviceCtx* ctx, int64_t n) {
   auto it = ctx->tuned_sum.find(size_class(n));
   if (it != ctx->tuned_sum.end()) return it->second;
-  // measured on GB300 (back-to-back launches): per-thread small superaccumulators
-  // win at every size; 256 x 4 is fastest below about 1e5 values (6.3-6.8 us),
-  // 384 x 4 up to about 1e7 (19.6 us at 1e7, where 384 x 6 takes 20.1), and
-  // 384 x 6 beyond (126.4 us on 1e8 values, 384 x 4 130.0, 384 x 8 137.6)
+  // Measured on GB300, back-to-back launches on the band input of 2^U(-60,60):
+  // per-thread small superaccumulators win below 2^25 values -- 256 x 4 below
+  // about 1e5 (6.3-6.8 us), 384 x 4 up to 2^25 (27.0 us at 2^24, where the
+  // large kernel takes 27.3) -- and the block-wide large superaccumulator
+  // (512 x 4) from 2^25 on: 46.1 against 49.4 us at 2^25, 120.6 against
+  // 127.4 us at 1e8 (384 x 6). On 1e8 values it stays within 117-121 us for
+  // a full exponent range, a constant array and one binade with either sign,
+  // but takes 135 us on normal deviates and 150 us on U(-1,1), where many
+  // lanes of a warp meet on a few chunks; xs_autotune_sum picks per input.
+  if (n < (int64_t(1) << 17)) return SumShape{XS_METHOD_SMALL, 256, 4};
+  if (n < (int64_t(1) << 25)) return SumShape{XS_METHOD_SMALL, 384, 4};
+  return SumShape{XS_METHOD_LARGE, 512, 4};
+}
+
+// Default launch shape of an explicitly chosen method (same measurements as
+// default_shape): the small kernel in its three size classes, the large one
+// in 512 x 4 at every size.
+SumShape method_shape(int method, int64_t n) {
+  if (method == XS_METHOD_LARGE) return SumShape{XS_METHOD_LARGE, 512, 4};
   if (n < (int64_t(1) << 17)) return SumShape{XS_METHOD_SMALL, 256, 4};
   if (n < (int64_t(1) << 25)) return SumShape{XS_METHOD_SMALL, 384, 4};
   return SumShape{XS_METHOD_SMALL, 384, 6};
@@ -682,12 +701,7 @@ xs_status xs_sum_async_config(const double* d_values, int64_t n, double* d_out, 
   if (!ctx) return st;
   SumShape shape = (method == XS_METHOD_AUTO) ? default_shape(ctx, n)
                                               : SumShape{method, block, unroll};
-  if (method != XS_METHOD_AUTO && (block == 0 || unroll == 0)) {
-    SumShape d = default_shape(ctx, n);
-    if (d.method != method) d = (method == XS_METHOD_SMALL) ? SumShape{method, 128, 4}
-                                                            : SumShape{method, 256, 4};
-    shape = d;
-  }
+  if (method != XS_METHOD_AUTO && (block == 0 || unroll == 0)) shape = method_shape(method, n);
   Workspace* w = workspace(ctx, s, &st);
   if (!w) return st;
   st = launch_sum(ctx, d_values, n, w->acc, d_out, 0, shape, grid, s);
@@ -833,9 +847,16 @@ xs_status xs_autotune_sum(const double* d_values, int64_t n, int reps, void* str
   if (!ctx) return st;
   Workspace* w = workspace(ctx, s, &st);
   if (!w) return st;
-  cudaEvent_t e0, e1;
-  XS_TRY_CUDA(cudaEventCreate(&e0));
-  XS_TRY_CUDA(cudaEventCreate(&e1));
+  struct Events {  // released on every return
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Events() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    }
+  } ev;
+  XS_TRY_CUDA(cudaEventCreate(&ev.e0));
+  XS_TRY_CUDA(cudaEventCreate(&ev.e1));
+  cudaEvent_t e0 = ev.e0, e1 = ev.e1;
   float best = 1e30f;
   SumShape win{XS_METHOD_SMALL, 128, 4};
   std::vector<float> times;
@@ -861,8 +882,6 @@ xs_status xs_autotune_sum(const double* d_values, int64_t n, int reps, void* str
       win = sh;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->tuned_sum[size_class(n)] = win;

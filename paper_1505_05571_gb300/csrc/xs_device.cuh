@@ -18,6 +18,7 @@
 // atomics (exact and order-free), and the last block to finish rounds.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -843,14 +844,17 @@ __device__ __noinline__ static unsigned long long warp_round_div(long long v0, l
 
 // Shared-memory layout: R copies of the lo and hi planes (lane L adds into
 // copy L mod R, so R times fewer lanes of a warp meet on one address when few
-// distinct exponents occur; each copy is shifted by 8 banks so the copies of
-// one chunk sit in different banks), one top plane for all copies, and the
-// per-warp transfer targets of the flush. A chunk's value is the sum over the
-// copies of hi:lo, plus top * 2^64.
+// distinct exponents occur; copy r starts r * kCopyWords words in, which puts
+// the copies of one chunk in different banks: shifts of 8 banks for up to 4
+// copies, of 5 for up to 6), one top plane for all copies, and the per-warp
+// transfer targets of the flush. A chunk's value is the sum over the copies
+// of hi:lo, plus top * 2^64.
 template <int NWARPS, int R>
 struct LargePlanes {
-  static constexpr int kCopyWords = 2 * kLChunks + 8;
-  unsigned copies[R * kCopyWords];
+  static_assert(R >= 1 && R <= 6, "copies of the planes");
+  static constexpr int kCopyWords = 2 * kLChunks + (R <= 4 ? 8 : 5);
+  static constexpr int kCopiesPadded = (R * kCopyWords + 3) / 4 * 4;  // keeps `top` 16-byte aligned
+  unsigned copies[kCopiesPadded];
   unsigned top[kLChunks];
   long long part[NWARPS][kSChunks];
   unsigned zeros[2];  // zero/subnormal terms of the block, by sign
@@ -890,28 +894,39 @@ __device__ __forceinline__ void large_add64(const LargeLane& L, unsigned ix, uns
 
 // Adds of one group of 2U terms (U 16-byte vectors). The low words of all
 // terms go first, so their atomics' returns are in flight together; then the
-// high words with the carries. When every lane's 2U terms share one index
-// (a constant array, say), each lane adds their sum once instead. Returns the
-// maximum over the terms of ((e - 1) mod 2048) << 20, which reaches
-// 0x7FE00000 exactly when some term has e == 0 or e == 2047 (the rare path).
+// high words with the carries. When all 2U terms of every lane of the warp
+// are normal and share one exponent (a constant array, or values of one
+// binade with either sign), each lane instead adds the net of its terms'
+// signed significands, |S| < 2U 2^53, once: into the positive chunk of that
+// exponent if S > 0, into the negative one if S < 0. Both chunks carry the
+// same weight with opposite signs and only their difference is ever used, so
+// the net leaves the sum unchanged, and lanes that meet on one word meet 2U
+// times less often. The test costs one logic op per term. Returns the maximum
+// over the terms of ((e - 1) mod 2048) << 20, which reaches 0x7FE00000
+// exactly when some term has e == 0 or e == 2047 (the rare path).
 template <int U>
 __device__ __forceinline__ unsigned large_group_add(const LargeLane& L, const ulonglong2* v) {
   unsigned ix[2 * U];
-  unsigned mx = 0u;
-  bool same = true;
+  unsigned mx = 0u, dx = 0u;
+  const unsigned h0 = (unsigned)(v[0].x >> 32);
 #pragma unroll
   for (int k = 0; k < 2 * U; ++k) {
     const unsigned h = (unsigned)(((k & 1) ? v[k >> 1].y : v[k >> 1].x) >> 32);
     ix[k] = h >> 20;
     mx = max(mx, (h - 0x00100000u) & 0x7FF00000u);
-    same = same && ix[k] == ix[0];
+    dx |= h ^ h0;
   }
-  if (__all_sync(kFull, same)) {
-    unsigned long long S = 0ull;  // below 2U 2^53
+  if (__all_sync(kFull, ((dx & 0x7FF00000u) | (mx >= 0x7FE00000u ? 1u : 0u)) == 0u)) {
+    long long S = 0;
 #pragma unroll
-    for (int k = 0; k < 2 * U; ++k)
-      S += (((k & 1) ? v[k >> 1].y : v[k >> 1].x) & kMantMask) | (1ull << 52);
-    large_add64(L, ix[0], S);
+    for (int k = 0; k < 2 * U; ++k) {
+      const unsigned long long b = (k & 1) ? v[k >> 1].y : v[k >> 1].x;
+      const long long M = (long long)((b & kMantMask) | (1ull << 52));
+      const long long sg = (long long)b >> 63;  // 0 or -1
+      S += (M ^ sg) - sg;
+    }
+    if (S != 0)
+      large_add64(L, (ix[0] & 0x7FFu) | (S < 0 ? 0x800u : 0u), (unsigned long long)(S < 0 ? -S : S));
     return mx;
   }
   unsigned v2[2 * U];
@@ -981,10 +996,12 @@ struct LargeThread {
 
 template <int NWARPS, int R>
 __device__ __forceinline__ void large_init(LargePlanes<NWARPS, R>& P, int tid, int nthreads) {
-  static_assert((R * LargePlanes<NWARPS, R>::kCopyWords + kLChunks) % 4 == 0, "uint4 clear");
+  // copies (padded to whole 16-byte vectors) and top are contiguous and 16-byte aligned
+  constexpr int W4 = (LargePlanes<NWARPS, R>::kCopiesPadded + kLChunks) / 4;
+  using Planes = LargePlanes<NWARPS, R>;
+  static_assert(offsetof(Planes, top) == 4 * Planes::kCopiesPadded, "planes are contiguous");
   uint4* w = reinterpret_cast<uint4*>(P.copies);
-  for (int k = tid; k < (R * LargePlanes<NWARPS, R>::kCopyWords + kLChunks) / 4; k += nthreads)
-    w[k] = make_uint4(0u, 0u, 0u, 0u);
+  for (int k = tid; k < W4; k += nthreads) w[k] = make_uint4(0u, 0u, 0u, 0u);
   long long* pp = &P.part[0][0];
   for (int k = tid; k < NWARPS * kSChunks; k += nthreads) pp[k] = 0;
   if (tid < 2) P.zeros[tid] = 0u;

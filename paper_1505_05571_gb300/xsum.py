@@ -176,6 +176,26 @@ def _ptr(x) -> int | None:
     raise TypeError(f"cannot take a pointer of {type(x)}")
 
 
+def _vals(x, n: int, itemsize: int = 8) -> int | None:
+    """Pointer of a values argument. When it is a tensor or an array, n items of
+    `itemsize` bytes must lie inside it (ValueError otherwise): a raw address
+    can carry no such check, so the library trusts n, and a kernel given an n
+    past the end of its buffer would read memory it does not own."""
+    if hasattr(x, "numel") and hasattr(x, "element_size"):
+        have = x.numel() * x.element_size()
+    elif hasattr(x, "nbytes") and hasattr(x, "ctypes"):
+        have = x.nbytes
+    else:
+        return _ptr(x)
+    if n * itemsize > have:  # (a negative n is the library's to reject)
+        raise ValueError(f"{n} values of {itemsize} bytes do not fit in a buffer of {have} bytes")
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("values must be contiguous")
+        return x.data_ptr()
+    return x.ctypes.data
+
+
 _torch = None
 
 
@@ -215,23 +235,23 @@ def xs_get_last_error() -> int:
 
 
 def xs_sum(d_values, n: int, stream=None) -> float:
-    return load().xs_sum(_ptr(d_values), n, _stream(stream))
+    return load().xs_sum(_vals(d_values, n), n, _stream(stream))
 
 
 def xs_sum_ex(d_values, n: int, stream=None) -> float:
     out = ctypes.c_double()
-    _check(load().xs_sum_ex(_ptr(d_values), n, _stream(stream), ctypes.byref(out)), "xs_sum_ex")
+    _check(load().xs_sum_ex(_vals(d_values, n), n, _stream(stream), ctypes.byref(out)), "xs_sum_ex")
     return out.value
 
 
 def xs_sum_async(d_values, n: int, d_out, method: int = XS_METHOD_AUTO, stream=None) -> None:
-    _check(load().xs_sum_async(_ptr(d_values), n, _ptr(d_out), method, _stream(stream)),
+    _check(load().xs_sum_async(_vals(d_values, n), n, _ptr(d_out), method, _stream(stream)),
            "xs_sum_async")
 
 
 def xs_sum_async_config(d_values, n: int, d_out, method: int, block: int, unroll: int,
                         grid: int = 0, stream=None) -> None:
-    _check(load().xs_sum_async_config(_ptr(d_values), n, _ptr(d_out), method, block, unroll, grid,
+    _check(load().xs_sum_async_config(_vals(d_values, n), n, _ptr(d_out), method, block, unroll, grid,
                                       _stream(stream)), "xs_sum_async_config")
 
 
@@ -258,7 +278,7 @@ def xs_list_configs() -> list[tuple[int, int, int]]:
 
 def xs_sum_host(h_values, n: int, stream=None) -> float:
     out = ctypes.c_double()
-    _check(load().xs_sum_host(_ptr(h_values), n, ctypes.byref(out), _stream(stream)), "xs_sum_host")
+    _check(load().xs_sum_host(_vals(h_values, n), n, ctypes.byref(out), _stream(stream)), "xs_sum_host")
     return out.value
 
 
@@ -266,25 +286,25 @@ XS_NOALLOC_MAX_TERMS = 1 << 45
 
 
 def xs_sum_noalloc(d_values, n: int, d_out, stream=None) -> None:
-    _check(load().xs_sum_noalloc(_ptr(d_values), n, _ptr(d_out), _stream(stream)),
+    _check(load().xs_sum_noalloc(_vals(d_values, n), n, _ptr(d_out), _stream(stream)),
            "xs_sum_noalloc")
 
 
 def xs_mean_async(d_values, n: int, d_out, stream=None) -> None:
-    _check(load().xs_mean_async(_ptr(d_values), n, _ptr(d_out), _stream(stream)), "xs_mean_async")
+    _check(load().xs_mean_async(_vals(d_values, n), n, _ptr(d_out), _stream(stream)), "xs_mean_async")
 
 
 def xs_dot_async(d_x, d_y, n: int, d_out, stream=None) -> None:
-    _check(load().xs_dot_async(_ptr(d_x), _ptr(d_y), n, _ptr(d_out), _stream(stream)),
+    _check(load().xs_dot_async(_vals(d_x, n), _vals(d_y, n), n, _ptr(d_out), _stream(stream)),
            "xs_dot_async")
 
 
 def xs_norm2_async(d_x, n: int, d_out, stream=None) -> None:
-    _check(load().xs_norm2_async(_ptr(d_x), n, _ptr(d_out), _stream(stream)), "xs_norm2_async")
+    _check(load().xs_norm2_async(_vals(d_x, n), n, _ptr(d_out), _stream(stream)), "xs_norm2_async")
 
 
 def xs_sum_f32_async(d_values, n: int, d_out, stream=None) -> None:
-    _check(load().xs_sum_f32_async(_ptr(d_values), n, _ptr(d_out), _stream(stream)),
+    _check(load().xs_sum_f32_async(_vals(d_values, n, 4), n, _ptr(d_out), _stream(stream)),
            "xs_sum_f32_async")
 
 
@@ -293,13 +313,13 @@ def xs_acc_round_div(h: int, divisor: int, d_out, stream=None) -> None:
 
 
 def xs_inexact_sum_async(d_values, n: int, d_out, stream=None) -> None:
-    _check(load().xs_inexact_sum_async(_ptr(d_values), n, _ptr(d_out), _stream(stream)),
+    _check(load().xs_inexact_sum_async(_vals(d_values, n), n, _ptr(d_out), _stream(stream)),
            "xs_inexact_sum_async")
 
 
 def xs_autotune_sum(d_values, n: int, reps: int = 5, stream=None):
     m, b, u, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
-    _check(load().xs_autotune_sum(_ptr(d_values), n, reps, _stream(stream), ctypes.byref(m),
+    _check(load().xs_autotune_sum(_vals(d_values, n), n, reps, _stream(stream), ctypes.byref(m),
                                   ctypes.byref(b), ctypes.byref(u), ctypes.byref(t)),
            "xs_autotune_sum")
     return {"method": m.value, "block": b.value, "unroll": u.value, "us": t.value}
@@ -379,7 +399,7 @@ def xs_acc_init(h: int, stream=None) -> None:
 
 
 def xs_acc_add(h: int, d_values, n: int, stream=None) -> None:
-    _check(load().xs_acc_add(h, _ptr(d_values), n, _stream(stream)), "xs_acc_add")
+    _check(load().xs_acc_add(h, _vals(d_values, n), n, _stream(stream)), "xs_acc_add")
 
 
 def xs_acc_merge(dst: int, src: int, stream=None) -> None:
@@ -444,7 +464,7 @@ def xs_server_open_session(server: int) -> int:
 
 
 def xs_server_submit(server: int, d_values, n: int, session: int = 0, flags: int = 0) -> int:
-    req = xs_request(session, _ptr(d_values), n, flags, 0)
+    req = xs_request(session, _vals(d_values, n), n, flags, 0)
     rid = ctypes.c_uint64()
     _check(load().xs_server_submit(server, ctypes.byref(req), ctypes.byref(rid)), "xs_server_submit")
     return rid.value

@@ -126,3 +126,27 @@ def test_argument_errors_come_before_any_device_work(lib_path):
     xsum.xs_sum_segments(0x1000, 0x2000, 0, 0x3000)
     # the blocking form reports through a quiet NaN and the thread's last error
     assert math.isnan(xsum.xs_sum(0x1000, -1)) and xsum.xs_get_last_error() == E_VAL
+
+
+def test_binding_rejects_counts_past_the_buffer(lib_path):
+    """Given a tensor or an array, the binding refuses an n whose values would
+    run past its end (raw addresses carry no extent, so the library cannot
+    check this itself); an n that fits goes through to the library."""
+    import numpy as np
+    import torch
+
+    from paper_1505_05571_gb300 import xsum
+
+    t = torch.zeros(10, dtype=torch.float64)
+    a = np.zeros(6, dtype=np.float64)
+    f = torch.zeros(9, dtype=torch.float32)
+    for call in (lambda: xsum.xs_sum_ex(t, 11), lambda: xsum.xs_sum_host(a, 7),
+                 lambda: xsum.xs_sum_async(t[2:], 9, 0x1000), lambda: xsum.xs_dot_async(t, t[1:], 10, 0x1000),
+                 lambda: xsum.xs_sum_f32_async(f, 10, 0x1000), lambda: xsum.xs_acc_add(0, t, 11),
+                 lambda: xsum.xs_sum_ex(torch.zeros(4, 4, dtype=torch.float64).t(), 16)):
+        with pytest.raises(ValueError):
+            call()
+    assert xsum.xs_sum_ex(t, 0) == 0.0  # fits: the library's empty sum
+    with pytest.raises(xsum.XsError) as e:
+        xsum.xs_sum_ex(t, -1)  # negative: the library's own error
+    assert e.value.status == xsum.XS_ERR_INVALID_VALUE

@@ -102,7 +102,11 @@ def test_noalloc_in_a_fresh_process_allocates_nothing():
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum():
+    # the library's own check, through a raw address (a tensor that small would
+    # already be refused by the binding, since n values do not fit in it)
     out = out_slot()
     with pytest.raises(xsum.XsError) as e:
-        xsum.xs_sum_noalloc(out, xsum.XS_NOALLOC_MAX_TERMS + 1, out)
+        xsum.xs_sum_noalloc(out.data_ptr(), xsum.XS_NOALLOC_MAX_TERMS + 1, out)
     assert e.value.status == xsum.XS_ERR_INVALID_VALUE
+    with pytest.raises(ValueError):
+        xsum.xs_sum_noalloc(out, 2, out)
