@@ -399,6 +399,19 @@ xs_status xs_debug_fail_allocation(int64_t k);
  * was. */
 int64_t xs_debug_live_allocations(void);
 
+/* 1 if this library was built with -DXS_DEBUG (build.py's debug build), else 0.
+ * In that build the kernels check their chunk indices (small accumulator
+ * chunks 0..66, large accumulator indices 0..4095, flushed pieces inside the
+ * small accumulator), the add bound between carry propagations (at most 2047
+ * adds, and every chunk within what they can reach) and the segmented tile
+ * table index; a failed check skips the access it guards and records a code. */
+int xs_is_debug_build(void);
+/* Waits for the device, then stores in *codes the OR of the codes recorded
+ * since the last call (1 small chunk index, 2 carry interval, 4 chunk bound,
+ * 8 large index, 16 flush index, 32 table index) and clears them. Always 0
+ * outside the debug build. XS_ERR_INVALID_POINTER if codes is NULL. */
+xs_status xs_debug_status(uint64_t* codes);
+
 #ifdef __cplusplus
 }
 #endif

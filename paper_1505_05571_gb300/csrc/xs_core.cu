@@ -62,6 +62,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   }
 
   const Split sp = split_input(a.x, a.n);
+  // the head and tail terms plus carry_tiles full tiles between propagations
+  XS_DCHECK(a.carry_tiles * 2 * UNROLL + 2 <= kCarryInterval, kDbgCarryInterval);
   constexpr long long TP = (long long)BLOCK * UNROLL;
   const long long ntiles = (sp.npairs + TP - 1) / TP;
   const long long nfull = sp.npairs / TP;  // tiles without a ragged end
@@ -1030,4 +1032,32 @@ xs_status xs_debug_fail_allocation(int64_t k) {
 
 int64_t xs_debug_live_allocations(void) { return g_live_allocs.load(); }
 
+int xs_is_debug_build(void) {
+#ifdef XS_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+xs_status xs_debug_status(uint64_t* codes) {
+  if (codes == nullptr) return set_error(XS_ERR_INVALID_POINTER);
+  *codes = 0;
+  if (!xs_is_debug_build()) return set_error(XS_OK);
+  unsigned long long all = 0ull, v = 0ull;
+  XS_TRY_CUDA(cudaDeviceSynchronize());
+  for (auto take : {debug_take_core, debug_take_segments, debug_take_serve, debug_take_dot,
+                    debug_take_f32, debug_take_noalloc}) {
+    XS_TRY_CUDA(take(&v));
+    all |= v;
+  }
+  *codes = all;
+  return set_error(XS_OK);
+}
+
 }  // extern "C"
+
+namespace xs {
+// This file's debug word (xs_debug_status).
+cudaError_t debug_take_core(unsigned long long* v) { return debug_word_take(v); }
+}  // namespace xs

@@ -37,6 +37,46 @@ constexpr unsigned long long kNegZero = 0x8000000000000000ull;
 constexpr unsigned long long kPayloadMask = 0x0007FFFFFFFFFFFFull;
 constexpr unsigned long long kMantMask = 0x000FFFFFFFFFFFFFull;
 
+// Debug build (-DXS_DEBUG): checks of the chunk indices and of the add bound
+// between carry propagations. A failed check ORs its code into this
+// translation unit's debug word and the access it guards is skipped, so a
+// broken invariant reaches the host (xs_debug_status) instead of touching
+// shared or global memory out of range. Without XS_DEBUG every check is the
+// constant true and compiles to nothing.
+enum : unsigned {
+  kDbgSmallIndex = 1u,     // small-accumulator chunk index past chunk 65 (an add writes i, i + 1)
+  kDbgCarryInterval = 2u,  // more adds between two propagations than the bound allows
+  kDbgChunkBound = 4u,     // a chunk outside what that bound lets it reach
+  kDbgLargeIndex = 8u,     // large-accumulator index past 4095
+  kDbgFlushIndex = 16u,    // a flushed chunk's pieces past the small accumulator's top
+  kDbgTableIndex = 32u,    // a segmented tile or slot index out of its table
+};
+#ifdef XS_DEBUG
+static __device__ unsigned long long d_xs_debug_word;
+__device__ __forceinline__ bool xs_dcheck(bool ok, unsigned code) {
+  if (!ok) atomicOr(&d_xs_debug_word, (unsigned long long)code);
+  return ok;
+}
+#define XS_DCHECK(cond, code) ::xs::xs_dcheck((cond), (code))
+// Reads and clears this translation unit's debug word (host).
+static inline cudaError_t debug_word_take(unsigned long long* v) {
+  cudaError_t e = cudaMemcpyFromSymbol(v, d_xs_debug_word, sizeof *v);
+  const unsigned long long zero = 0ull;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(d_xs_debug_word, &zero, sizeof zero);
+  return e;
+}
+#else
+#define XS_DCHECK(cond, code) true
+static inline cudaError_t debug_word_take(unsigned long long* v) {
+  *v = 0ull;
+  return cudaSuccess;
+}
+#endif
+// A bound on a small-accumulator chunk between propagations: below 2^32 after
+// one, then at most kCarryInterval adds of a low part (< 2^32) or a high part
+// (< 2^52), each possibly negated.
+constexpr long long kChunkBound = (1ll << 32) + (long long)kCarryInterval * ((1ll << 52) + (1ll << 32));
+
 // Record of the terms that do not enter the chunks (Inf and NaN fields of the
 // small superaccumulator, Fig. 3) plus what decides the sign of a zero.
 enum : unsigned {
@@ -128,6 +168,7 @@ __device__ __forceinline__ void sacc_add(long long* __restrict__ a, int stride,
   const long long s = (long long)((int)hi >> 31);  // 0 or -1
   const long long vlo = (long long)(unsigned long long)p0;
   const long long vhi = (long long)(((unsigned long long)q1 << 32) | q0);
+  if (!XS_DCHECK(i + 1u < (unsigned)kSChunks, kDbgSmallIndex)) return;
   long long* c = a + (int)i * stride;
   c[0] += (vlo ^ s) - s;
   c[stride] += (vhi ^ s) - s;
@@ -149,6 +190,7 @@ __device__ __forceinline__ void sacc_add_normal(long long* __restrict__ a, unsig
   const unsigned long long Q = (unsigned long long)mh * pw + (P >> 32);  // (M << l) >> 32
   const unsigned s = (unsigned)((int)hi >> 31);       // 0 or 0xFFFFFFFF
   const unsigned s1 = hi >> 31;                       // 0 or 1
+  if (!XS_DCHECK((e >> kLowExpBits) + 1u < (unsigned)kSChunks, kDbgSmallIndex)) return;
   long long* c = a + (int)(e >> kLowExpBits) * STRIDE;
   const unsigned long long x0 = ((unsigned long long)s << 32) | ((unsigned)P ^ s);
   const unsigned long long x1 = Q ^ (((unsigned long long)s << 32) | s);
@@ -308,6 +350,7 @@ __device__ __forceinline__ void sacc_propagate(long long* __restrict__ a, int st
   long long carry = 0;
 #pragma unroll 6
   for (int c = 0; c < kSChunks - 1; ++c) {
+    XS_DCHECK(a[c * stride] <= kChunkBound && a[c * stride] >= -kChunkBound, kDbgChunkBound);
     const long long v = a[c * stride] + carry;
     a[c * stride] = v & 0xFFFFFFFFll;
     carry = v >> 32;
@@ -882,6 +925,7 @@ struct LargeLane {
 // value, the high word with the carry out of it, and a carry out of the high
 // word into the top plane.
 __device__ __forceinline__ void large_add64(const LargeLane& L, unsigned ix, unsigned long long S) {
+  if (!XS_DCHECK(ix < (unsigned)kLChunks, kDbgLargeIndex)) return;
   const unsigned l = (unsigned)S;
   const unsigned old = atom_add_shared(L.lo + (ix << 2), l);
   unsigned sum, hi;
@@ -913,6 +957,7 @@ __device__ __forceinline__ unsigned large_group_add(const LargeLane& L, const ul
   for (int k = 0; k < 2 * U; ++k) {
     const unsigned h = (unsigned)(((k & 1) ? v[k >> 1].y : v[k >> 1].x) >> 32);
     ix[k] = h >> 20;
+    if (!XS_DCHECK(ix[k] < (unsigned)kLChunks, kDbgLargeIndex)) ix[k] &= kLChunks - 1;
     mx = max(mx, (h - 0x00100000u) & 0x7FF00000u);
     dx |= h ^ h0;
   }
@@ -1043,6 +1088,7 @@ __device__ __forceinline__ void large_flush(LargePlanes<NWARPS, R>& P) {
     const unsigned ee = e ? e : 1u;
     V <<= (ee & 31u);
     const int i = (int)(ee >> kLowExpBits);  // the same for the whole run
+    if (!XS_DCHECK(i + 3 < kSChunks, kDbgFlushIndex)) continue;  // uniform over the warp
     const bool neg = (ix >> 11) != 0u;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {

@@ -248,3 +248,8 @@ xs_status xs_norm2_async(const double* d_x, int64_t n, double* d_out, void* stre
 }
 
 }  // extern "C"
+
+namespace xs {
+// This file's debug word (xs_debug_status).
+cudaError_t debug_take_dot(unsigned long long* v) { return debug_word_take(v); }
+}  // namespace xs

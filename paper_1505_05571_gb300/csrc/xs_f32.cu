@@ -373,3 +373,8 @@ extern "C" xs_status xs_sum_f32_async(const float* d_values, int64_t n, float* d
   XS_TRY_CUDA(launch_pdl(k_sum_f32<kF32Block, kF32Unroll>, (unsigned)g, (unsigned)kF32Block, smem, s, a));
   return set_error(XS_OK);
 }
+
+namespace xs {
+// This file's debug word (xs_debug_status).
+cudaError_t debug_take_f32(unsigned long long* v) { return debug_word_take(v); }
+}  // namespace xs

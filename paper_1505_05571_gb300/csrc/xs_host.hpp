@@ -40,6 +40,15 @@ cudaError_t host_alloc(T** p, size_t bytes, unsigned flags) {
   return host_alloc(reinterpret_cast<void**>(p), bytes, flags);
 }
 
+// Each translation unit's debug word, read and cleared (always 0 outside a
+// -DXS_DEBUG build): the codes of the checks its kernels saw fail.
+cudaError_t debug_take_core(unsigned long long* v);
+cudaError_t debug_take_segments(unsigned long long* v);
+cudaError_t debug_take_serve(unsigned long long* v);
+cudaError_t debug_take_dot(unsigned long long* v);
+cudaError_t debug_take_f32(unsigned long long* v);
+cudaError_t debug_take_noalloc(unsigned long long* v);
+
 // Device pointer check (cudaPointerGetAttributes): host or unregistered
 // memory is rejected.
 xs_status check_device_ptr(const void* p);

@@ -76,3 +76,8 @@ extern "C" xs_status xs_sum_noalloc(const double* d_values, int64_t n, double* d
   if ((st = launch_small_fixed(d_values, n, acc, d_out, grid, s)) != XS_OK) return st;
   return set_error(XS_OK);
 }
+
+namespace xs {
+// This file's debug word (xs_debug_status).
+cudaError_t debug_take_noalloc(unsigned long long* v) { return debug_word_take(v); }
+}  // namespace xs

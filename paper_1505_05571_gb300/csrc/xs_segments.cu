@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
   // behind the previous merge.
   // segment of tile t: from the table, else the last s with tile_start[s] <= t
   auto segment_of = [&](long long t) -> long long {
-    if (ntiles <= a.tile_cap) return a.tile_seg[t];
+    if (ntiles <= a.tile_cap && XS_DCHECK(t >= 0 && t < ntiles, kDbgTableIndex)) return a.tile_seg[t];
     long long lo_s = 0, hi_s = a.nseg;  // invariant: tile_start[lo_s] <= t < tile_start[hi_s]
     while (hi_s - lo_s > 1) {
       const long long mid = (lo_s + hi_s) >> 1;
@@ -903,3 +903,8 @@ xs_status xs_autotune_segments(const double* d_values, const int64_t* d_offsets,
 }
 
 }  // extern "C"
+
+namespace xs {
+// This file's debug word (xs_debug_status).
+cudaError_t debug_take_segments(unsigned long long* v) { return debug_word_take(v); }
+}  // namespace xs

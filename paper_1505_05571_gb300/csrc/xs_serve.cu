@@ -805,3 +805,8 @@ xs_status xs_server_destroy(xs_server s) {
 }
 
 }  // extern "C"
+
+namespace xs {
+// This file's debug word (xs_debug_status).
+cudaError_t debug_take_serve(unsigned long long* v) { return debug_word_take(v); }
+}  // namespace xs

@@ -136,6 +136,8 @@ _SIGS = {
     "xs_acc_device_state": (_vp, [_vp]),
     "xs_debug_fail_allocation": (ctypes.c_int, [_c_int64]),
     "xs_debug_live_allocations": (_c_int64, []),
+    "xs_is_debug_build": (ctypes.c_int, []),
+    "xs_debug_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 _lib = None
@@ -437,6 +439,17 @@ def xs_debug_fail_allocation(k: int) -> None:
 
 def xs_debug_live_allocations() -> int:
     return load().xs_debug_live_allocations()
+
+
+def xs_is_debug_build() -> bool:
+    return bool(load().xs_is_debug_build())
+
+
+def xs_debug_status() -> int:
+    """OR of the check codes the debug build's kernels recorded since the last call."""
+    v = ctypes.c_uint64()
+    _check(load().xs_debug_status(ctypes.byref(v)), "xs_debug_status")
+    return v.value
 
 
 def acc_state_chunks(state: bytes) -> list[int]:

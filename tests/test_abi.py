@@ -150,3 +150,12 @@ def test_binding_rejects_counts_past_the_buffer(lib_path):
     with pytest.raises(xsum.XsError) as e:
         xsum.xs_sum_ex(t, -1)  # negative: the library's own error
     assert e.value.status == xsum.XS_ERR_INVALID_VALUE
+
+
+def test_release_build_has_no_debug_checks(lib_path):
+    """The release library reports itself as such, and its debug status is 0
+    without any device call."""
+    from paper_1505_05571_gb300 import xsum
+
+    assert not xsum.xs_is_debug_build()
+    assert xsum.xs_debug_status() == 0
