@@ -3,7 +3,8 @@
     python -m workloads.cases <case> [--reps N] [--prefetch TILES]
 
 Cases: sum_cfg1 (the default method), small_cfg1 and large_cfg1 (each method
-explicitly), sum_cfg2a (2^28 doubles, full exponent range), mean_cfg1, dot_cfg1, norm2_cfg1, f32_2e8,
+explicitly), sum_cfg2a (2^28 doubles, full exponent range) and small_cfg2a (the same
+with the small method), mean_cfg1, dot_cfg1, norm2_cfg1, f32_2e8,
 seg_cfg3_5k (5,000 segments of the config-3 length law), seg_tiny (2,000,000
 segments of 1..100 values). Inputs are generated on the device; the case prints
 its median CUDA-event time. This module only calls the library.
@@ -20,7 +21,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-CASES = ("sum_cfg1", "small_cfg1", "sum_cfg2a", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1", "f32_2e8",
+CASES = ("sum_cfg1", "small_cfg1", "sum_cfg2a", "small_cfg2a", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1", "f32_2e8",
          "seg_cfg3_5k", "seg_tiny")
 
 
@@ -35,11 +36,12 @@ def build_case(name: str):
 
     dev = torch.device("cuda", 0)
     out = torch.empty(1, dtype=torch.float64, device=dev)
-    if name == "sum_cfg2a":  # exponents uniform over the full range, subnormals included
+    if name in ("sum_cfg2a", "small_cfg2a"):  # exponents uniform over the full range, subnormals included
         n = 1 << 28
         x = torch.empty(n, dtype=torch.int64, device=dev)
         devgen.full_range(x, 0, 0)
-        return (lambda: xsum.xs_sum_async(x.view(torch.float64), n, out)), 8 * n, (x,)
+        m = xsum.XS_METHOD_AUTO if name == "sum_cfg2a" else xsum.XS_METHOD_SMALL
+        return (lambda: xsum.xs_sum_async(x.view(torch.float64), n, out, m)), 8 * n, (x,)
     if name in ("sum_cfg1", "small_cfg1", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1"):
         n = 10 ** 8
         x = torch.empty(n, dtype=torch.int64, device=dev)
