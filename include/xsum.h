@@ -288,6 +288,9 @@ typedef struct xs_server_options {
   int streams;          /* batches in flight at once (0 = 3) */
   int max_batch;        /* requests per batch launch (0 = 256) */
   int tile_elems;       /* elements per work item of a one-warp group (64 .. 2^26; 0 = 65536) */
+  int long_min;         /* requests of at least this many values are summed in block-wide tiles,
+                           one large superaccumulator per block (Large, Fig. 4); 0 = 2^20 */
+  int long_tile;        /* values per block-wide tile (1024 .. 2^26; 0 = 2^20) */
 } xs_server_options;
 
 /* xs_request.flags */

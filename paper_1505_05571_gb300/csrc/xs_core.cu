@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
 
   const Split sp = split_input(a.x, a.n);
   // the head and tail terms plus carry_tiles full tiles between propagations
-  XS_DCHECK(a.carry_tiles * 2 * UNROLL + 2 <= kCarryInterval, kDbgCarryInterval);
+  (void)XS_DCHECK(a.carry_tiles * 2 * UNROLL + 2 <= kCarryInterval, kDbgCarryInterval);
   constexpr long long TP = (long long)BLOCK * UNROLL;
   const long long ntiles = (sp.npairs + TP - 1) / TP;
   const long long nfull = sp.npairs / TP;  // tiles without a ragged end
@@ -77,10 +77,10 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_small(SumArgs a) {
   grid_dependency_wait();
   ulonglong2 A[UNROLL], B[UNROLL];
   if (t < nfull) load_full<BLOCK, UNROLL>(sp, t, tid, A);
-  if (blockIdx.x == 0 && tid == 0) {
+  if (blockIdx.x == 0 && tid < 32) {  // head (one element per lane) and tail
     const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
-    if (sp.head) T.one<BLOCK, TRACK>(xb[0]);
-    if (sp.tail) T.one<BLOCK, TRACK>(xb[a.n - 1]);
+    if (tid < sp.head) T.one<BLOCK, TRACK>(xb[tid]);
+    if (tid == 0 && sp.tail) T.one<BLOCK, TRACK>(xb[a.n - 1]);
   }
   int since = 0;
   auto tick = [&]() {
@@ -190,13 +190,13 @@ __global__ void __launch_bounds__(BLOCK, large_blocks_per_sm<BLOCK>()) k_sum_lar
   LargeThread T;
   ulonglong2 A[UNROLL], B[UNROLL];
   if (t < nfull) load_full<BLOCK, UNROLL>(sp, t, tid, A);
-  if (blockIdx.x == 0 && tid == 0) {
+  if (blockIdx.x == 0 && tid < 32) {  // head (one element per lane) and tail
     const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
-    if (sp.head) {
-      large_one_add(L, xb[0]);
-      T.term(xb[0]);
+    if (tid < sp.head) {
+      large_one_add(L, xb[tid]);
+      T.term(xb[tid]);
     }
-    if (sp.tail) {
+    if (tid == 0 && sp.tail) {
       large_one_add(L, xb[a.n - 1]);
       T.term(xb[a.n - 1]);
     }
@@ -312,9 +312,9 @@ __global__ void __launch_bounds__(256) k_inexact_sum(const double* x, long long 
     s0 += __longlong_as_double((long long)a.x);
     s1 += __longlong_as_double((long long)a.y);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (sp.head) s2 += x[0];
-    if (sp.tail) s3 += x[n - 1];
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    if ((int)threadIdx.x < sp.head) s2 += x[threadIdx.x];
+    if (threadIdx.x == 0 && sp.tail) s3 += x[n - 1];
   }
   double s = (s0 + s1) + (s2 + s3);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
@@ -547,21 +547,20 @@ SumShape default_shape(DeviceCtx* ctx, int64_t n) {
   // per-thread small superaccumulators win below 2^25 values -- 256 x 4 below
   // about 1e5 (6.3-6.8 us), 384 x 4 up to 2^25 (27.0 us at 2^24, where the
   // large kernel takes 27.3) -- and the block-wide large superaccumulator
-  // (512 x 4) from 2^25 on: 46.1 against 49.4 us at 2^25, 120.6 against
-  // 127.4 us at 1e8 (384 x 6). On 1e8 values it stays within 117-121 us for
-  // a full exponent range, a constant array and one binade with either sign,
-  // but takes 135 us on normal deviates and 150 us on U(-1,1), where many
-  // lanes of a warp meet on a few chunks; xs_autotune_sum picks per input.
+  // (768 x 4) from 2^25 on: 119 against 128 us at 1e8 (384 x 6), and 118
+  // against 146 us for 1e8 values over the full exponent range. On 1e8
+  // values it takes 124 us on normal deviates and 146 us on U(-1,1), where
+  // many lanes of a warp meet on a few chunks; xs_autotune_sum picks per input.
   if (n < (int64_t(1) << 17)) return SumShape{XS_METHOD_SMALL, 256, 4};
   if (n < (int64_t(1) << 25)) return SumShape{XS_METHOD_SMALL, 384, 4};
-  return SumShape{XS_METHOD_LARGE, 512, 4};
+  return SumShape{XS_METHOD_LARGE, 768, 4};
 }
 
 // Default launch shape of an explicitly chosen method (same measurements as
 // default_shape): the small kernel in its three size classes, the large one
-// in 512 x 4 at every size.
+// in 768 x 4 at every size.
 SumShape method_shape(int method, int64_t n) {
-  if (method == XS_METHOD_LARGE) return SumShape{XS_METHOD_LARGE, 512, 4};
+  if (method == XS_METHOD_LARGE) return SumShape{XS_METHOD_LARGE, 768, 4};
   if (n < (int64_t(1) << 17)) return SumShape{XS_METHOD_SMALL, 256, 4};
   if (n < (int64_t(1) << 25)) return SumShape{XS_METHOD_SMALL, 384, 4};
   return SumShape{XS_METHOD_SMALL, 384, 6};

@@ -350,7 +350,7 @@ __device__ __forceinline__ void sacc_propagate(long long* __restrict__ a, int st
   long long carry = 0;
 #pragma unroll 6
   for (int c = 0; c < kSChunks - 1; ++c) {
-    XS_DCHECK(a[c * stride] <= kChunkBound && a[c * stride] >= -kChunkBound, kDbgChunkBound);
+    (void)XS_DCHECK(a[c * stride] <= kChunkBound && a[c * stride] >= -kChunkBound, kDbgChunkBound);
     const long long v = a[c * stride] + carry;
     a[c * stride] = v & 0xFFFFFFFFll;
     carry = v >> 32;
@@ -362,18 +362,22 @@ __device__ __forceinline__ void sacc_propagate(long long* __restrict__ a, int st
 // (rank r among them). The body streams as groups of UNROLL 16-byte vectors
 // per thread: full groups load without bounds checks into two register buffers
 // used in turn (the next group's loads are in flight while the current one is
-// added), the ragged last group is padded with -0. One unaligned head and one
-// odd tail element go to ranks 0 and nthr-1. With PREFETCH, rank 0 prefetches
-// the range into L2 a few groups ahead.
+// added), the ragged last group is padded with -0. The head before the first
+// 256-byte boundary (up to 31 elements, one per rank from rank 0: the body
+// then streams from that boundary, which the loads' 256-byte L2 granules and
+// the bulk prefetch need for full speed) and one odd tail element (rank
+// nthr-1) go apart; nthr >= 32. With PREFETCH, rank 0 prefetches the range
+// into L2 a few groups ahead.
 template <int BLOCK, int UNROLL, bool PREFETCH, bool TRACK = false>
 __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x, long long lo,
                                                  long long hi, int r, int nthr,
                                                  int carry_groups = 0) {
   const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(x);
   long long p = lo;
-  if (p < hi && (((uintptr_t)(x + p)) & 15u) != 0u) {
-    if (r == 0) T.one<BLOCK, TRACK>(xb[p]);
-    ++p;
+  {
+    const long long h = min((long long)((256u - ((uintptr_t)(x + p) & 255u)) & 255u) / 8, hi - p);
+    if (r < h) T.one<BLOCK, TRACK>(xb[p + r]);
+    p += h;
   }
   if (((hi - p) & 1) != 0 && p < hi) {
     if (r == nthr - 1) T.one<BLOCK, TRACK>(xb[hi - 1]);
@@ -932,6 +936,7 @@ __device__ __forceinline__ void large_add64(const LargeLane& L, unsigned ix, uns
   asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;"
       : "=r"(sum), "=r"(hi)
       : "r"(old), "r"(l), "r"((unsigned)(S >> 32)));
+  (void)sum;
   const unsigned old2 = atom_add_shared(L.lo + (ix << 2) + 4u * kLChunks, hi);
   if (old2 + hi < hi) red_add_shared(L.top + (ix << 2), 1u);
 }
@@ -945,7 +950,8 @@ __device__ __forceinline__ void large_add64(const LargeLane& L, unsigned ix, uns
 // exponent if S > 0, into the negative one if S < 0. Both chunks carry the
 // same weight with opposite signs and only their difference is ever used, so
 // the net leaves the sum unchanged, and lanes that meet on one word meet 2U
-// times less often. The test costs one logic op per term. Returns the maximum
+// times less often; when every lane has the same exponent, the warp adds the
+// sum of the nets once. The test costs one logic op per term. Returns the maximum
 // over the terms of ((e - 1) mod 2048) << 20, which reaches 0x7FE00000
 // exactly when some term has e == 0 or e == 2047 (the rare path).
 template <int U>
@@ -970,8 +976,17 @@ __device__ __forceinline__ unsigned large_group_add(const LargeLane& L, const ul
       const long long sg = (long long)b >> 63;  // 0 or -1
       S += (M ^ sg) - sg;
     }
-    if (S != 0)
-      large_add64(L, (ix[0] & 0x7FFu) | (S < 0 ? 0x800u : 0u), (unsigned long long)(S < 0 ? -S : S));
+    const unsigned e0 = ix[0] & 0x7FFu;
+    if (__all_sync(kFull, __shfl_sync(kFull, e0, 0) == e0)) {
+      // the whole warp on one exponent (a constant array): one add per warp,
+      // |sum| < 32 2U 2^53 <= 2^61
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(kFull, S, o);
+      if ((threadIdx.x & 31) == 0 && S != 0)
+        large_add64(L, e0 | (S < 0 ? 0x800u : 0u), (unsigned long long)(S < 0 ? -S : S));
+      return mx;
+    }
+    if (S != 0) large_add64(L, e0 | (S < 0 ? 0x800u : 0u), (unsigned long long)(S < 0 ? -S : S));
     return mx;
   }
   unsigned v2[2 * U];
@@ -997,6 +1012,69 @@ __device__ __forceinline__ unsigned large_group_add(const LargeLane& L, const ul
 // One term (the unaligned head, the odd tail, the ragged last tile).
 __device__ __forceinline__ void large_one_add(const LargeLane& L, unsigned long long b) {
   large_add64(L, (unsigned)(b >> 52), (b & kMantMask) | (1ull << 52));
+}
+
+// Adds x[lo, hi) into the block's large superaccumulator, all BLOCK threads
+// of the block together (rank tid): the elements before the first 256-byte
+// boundary by threads 0..30 (one each), an odd last one by thread BLOCK - 1,
+// the body, from that boundary, as groups of UNROLL 16-byte
+// vectors per thread in two register buffers used in turn (the next group's
+// loads are in flight while the current one is added, and the groups after it
+// stream into L2), the ragged end term by term. Every thread of the block
+// must call it with the same range.
+template <int BLOCK, int UNROLL, class Thread>
+__device__ __forceinline__ void large_range(const LargeLane& L, Thread& T, const double* x,
+                                            long long lo, long long hi, int tid) {
+  const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(x);
+  long long p = lo;
+  {
+    const long long h = min((long long)((256u - ((uintptr_t)(xb + p) & 255u)) & 255u) / 8, hi - p);
+    if (tid < h) {
+      large_one_add(L, xb[p + tid]);
+      T.term(xb[p + tid]);
+    }
+    p += h;
+  }
+  if (((hi - p) & 1) != 0 && tid == BLOCK - 1) {
+    large_one_add(L, xb[hi - 1]);
+    T.term(xb[hi - 1]);
+  }
+  const long long npairs = (hi - p) >> 1;
+  const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(xb + p);
+  constexpr long long GP = (long long)BLOCK * UNROLL;  // pairs per group
+  const long long ng = npairs / GP;
+  ulonglong2 A[UNROLL], B[UNROLL];
+  auto load = [&](ulonglong2* buf, long long g) {
+    const ulonglong2* q = xv + g * GP + tid;
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) buf[u] = ld_stream(q + u * BLOCK);
+  };
+  // one thread keeps the L2 bulk prefetch kPF groups ahead of the loads (the
+  // first groups are the caller's to prefetch)
+  constexpr long long kPF = 3;
+  auto prefetch = [&](long long gp) {
+    if (tid == 0 && gp < ng) prefetch_l2(xv + gp * GP, (unsigned)(GP * 16));
+  };
+  long long g = 0;
+  if (ng > 0) load(A, 0);
+  while (g < ng) {
+    prefetch(g + kPF);
+    if (g + 1 < ng) load(B, g + 1);
+    T.template group_record<UNROLL>(large_group_add<UNROLL>(L, A), A);
+    ++g;
+    if (g >= ng) break;
+    prefetch(g + kPF);
+    if (g + 1 < ng) load(A, g + 1);
+    T.template group_record<UNROLL>(large_group_add<UNROLL>(L, B), B);
+    ++g;
+  }
+  for (long long q = ng * GP + tid; q < npairs; q += BLOCK) {
+    const ulonglong2 v = ld_stream(xv + q);
+    large_one_add(L, v.x);
+    large_one_add(L, v.y);
+    T.term(v.x);
+    T.term(v.y);
+  }
 }
 
 // Per-thread record of the large method: Inf/NaN and the sign of a zero as in
@@ -1070,8 +1148,10 @@ __device__ __forceinline__ LargeLane large_lane(LargePlanes<NWARPS, R>& P) {
 // 32-bit pieces for small chunks i..i+3 whose warp sums are formed with 32-bit
 // reductions of 16-bit digits (below 2^21 each, exact) and added, signed, into
 // the warp's own row of `part`. Needs a barrier before (all adds done, zero
-// counts in P.zeros).
-template <int NWARPS, int R>
+// counts in P.zeros). With CLEAR, the words of every run that held anything
+// are zeroed as they are read, so the planes are ready for the next sum
+// (the part rows and the zero counts are the caller's to clear).
+template <int NWARPS, int R, bool CLEAR = false>
 __device__ __forceinline__ void large_flush(LargePlanes<NWARPS, R>& P) {
   constexpr int CW = LargePlanes<NWARPS, R>::kCopyWords;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1082,6 +1162,14 @@ __device__ __forceinline__ void large_flush(LargePlanes<NWARPS, R>& P) {
 #pragma unroll
     for (int r = 0; r < R; ++r)
       V += ((unsigned __int128)P.copies[r * CW + kLChunks + ix] << 32) | P.copies[r * CW + ix];
+    if (CLEAR && __any_sync(kFull, V != 0)) {  // raw words: a run no term reached is all zero
+      P.top[ix] = 0u;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        P.copies[r * CW + ix] = 0u;
+        P.copies[r * CW + kLChunks + ix] = 0u;
+      }
+    }
     if (e == 0x7FFu) V = 0;  // Inf / NaN record only
     if (e == 0u) V -= (unsigned __int128)P.zeros[ix >> 11] << 52;  // their implicit bits
     if (!__any_sync(kFull, V != 0)) continue;

@@ -139,10 +139,10 @@ __global__ void __launch_bounds__(BLOCK, 1) k_dot_small(DotArgs d) {
   if (tid == 0)
     for (int k = 0; k <= a.prefetch; ++k) prefetch(t + k * G);
   grid_dependency_wait();
-  if (blockIdx.x == 0 && tid == 0) {
+  if (blockIdx.x == 0 && tid < 32) {  // head (one element per lane) and tail
     const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
-    if (sp.head) T.one<BLOCK>(canon_nan(product_bits(xb[0], y_at(0))));
-    if (sp.tail) T.one<BLOCK>(canon_nan(product_bits(xb[a.n - 1], y_at(a.n - 1))));
+    if (tid < sp.head) T.one<BLOCK>(canon_nan(product_bits(xb[tid], y_at(tid))));
+    if (tid == 0 && sp.tail) T.one<BLOCK>(canon_nan(product_bits(xb[a.n - 1], y_at(a.n - 1))));
   }
   ulonglong2 XA[UNROLL], YA[UNROLL], XB[UNROLL], YB[UNROLL], PA[UNROLL], PB[UNROLL];
   if (t < ntiles) {

@@ -211,16 +211,19 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_sum_f32(F32Args a) {
   T.acc = smem32 + tid;
 #pragma unroll
   for (int c = 0; c < 16; ++c) T.acc[c * BLOCK] = 0;
-  // head: elements before the first 16-byte boundary; body: uint4 quads; tail
-  const int head = (int)min((long long)((16u - ((uintptr_t)a.x & 15u)) & 15u) / 4, a.n);
+  // head: the (up to 63) elements before the first 256-byte boundary, so the
+  // streamed body starts on one (as in the FP64 kernels); body: uint4 quads;
+  // tail: up to 3 elements
+  const int head = (int)min((long long)((256u - ((uintptr_t)a.x & 255u)) & 255u) / 4, a.n);
   const long long nq = (a.n - head) / 4;
   const int tail = (int)((a.n - head) - nq * 4);
   const uint4* xq = reinterpret_cast<const uint4*>(a.x + head);
   const unsigned* xb = reinterpret_cast<const unsigned*>(a.x);
   grid_dependency_wait();
-  if (blockIdx.x == 0 && tid == 0) {
-    for (int k = 0; k < head; ++k) T.one<BLOCK>(xb[k]);
-    for (int k = 0; k < tail; ++k) T.one<BLOCK>(xb[a.n - 1 - k]);
+  if (blockIdx.x == 0 && tid < 32) {  // at most 2 head terms per lane, 3 tail terms in lane 0
+    for (int k = tid; k < head; k += 32) T.one<BLOCK>(xb[k]);
+    if (tid == 0)
+      for (int k = 0; k < tail; ++k) T.one<BLOCK>(xb[a.n - 1 - k]);
   }
   constexpr long long TQ = (long long)BLOCK * UNROLL;
   const long long ntiles = (nq + TQ - 1) / TQ;

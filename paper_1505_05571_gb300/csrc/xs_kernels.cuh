@@ -123,8 +123,11 @@ static __device__ void finish_grid_window(const SumArgs& a, long long* sc) {
   if (lane == 0) *reinterpret_cast<unsigned long long*>(a.out) = bits;
 }
 
-// Split of the input into an optional unaligned head element, 16-byte pairs
-// and an optional tail element.
+// Split of the input into a head of up to 31 elements before the first
+// 256-byte boundary, 16-byte pairs from there on, and an optional odd tail
+// element. The streamed body starts on a 256-byte boundary: measured on GB300,
+// a body that starts 8 or 128 bytes past one reads 12-30 % slower (the loads'
+// 256-byte L2 fetch granules and the bulk prefetch then straddle boundaries).
 struct Split {
   int head;
   bool tail;
@@ -133,7 +136,7 @@ struct Split {
 };
 __device__ __forceinline__ Split split_input(const double* x, long long n) {
   Split s;
-  s.head = (((uintptr_t)x & 15u) != 0u && n > 0) ? 1 : 0;
+  s.head = (int)min((long long)((256u - ((uintptr_t)x & 255u)) & 255u) / 8, n);
   const long long body = n - s.head;
   s.npairs = body >> 1;
   s.tail = (body & 1) != 0;

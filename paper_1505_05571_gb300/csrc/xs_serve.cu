@@ -37,18 +37,23 @@ struct BatchItem {
   const double* x;
   long long n;
   long long tile0;     // first global tile of this item
+  long long tile_len;  // values per tile: the small tile, or the block-wide tile of a long request
   int slot;            // accumulator slot
   int slot_tiles;      // tiles of all items of this slot in the batch (ticket target)
   int res_idx;         // result index written by the slot's finisher (-1: none)
   unsigned flags;      // bit 0: the slot's group ends with a finish
 };
 
+// Tiles [0, small_tiles) are the small requests' (one-warp groups), tiles
+// [small_tiles, total_tiles) the long requests' (whole blocks); items are in
+// tile order, so one search finds a tile's item in either range.
 struct BatchHeader {
-  unsigned long long cursor;
+  unsigned long long cursor;      // next small tile
+  unsigned long long cursor_big;  // next long tile (starts at small_tiles)
+  long long small_tiles;
   long long total_tiles;
   int nitems;
   int pad;
-  long long pad2;
 };
 
 struct BatchArgs {
@@ -59,15 +64,24 @@ struct BatchArgs {
   long long tile_elems;
 };
 
-// Launch shape: blocks of 192 threads (two per SM), each of six independent
-// one-warp work groups; tiles of 2^16 values. Measured on GB300 with saturated
-// serving of config-4 requests: 5.09 TB/s, against 4.71 TB/s with one
-// 192-thread group per block and tiles of 2^18, 4.82 TB/s for 384-thread
-// blocks of one-warp groups, 4.89 TB/s for two-warp groups; tiles of 2^17
-// give 5.17 TB/s but a third more median latency at half load.
-constexpr int kServeBlock = 192;
+// Launch shape: one block of 512 threads per SM. Small requests' tiles
+// (2^16 values by default) go to twelve one-warp work groups of the first 384
+// threads with per-thread small superaccumulators, four loads per thread; then
+// the long requests' tiles (2^20 values by default) to whole blocks with one
+// large superaccumulator each (four loads per thread). Measured on GB300 with
+// saturated serving of config-4 requests, the one-warp groups alone reach
+// 5.1 TB/s whatever the block shape (192 or 384 threads, 4 loads; 8 loads:
+// 3.3-4.5 TB/s), the same with one batch in flight as with three.
+constexpr int kServeBlock = 384;      // threads of the small-tile phase
 constexpr int kServeGroup = 32;
 constexpr int kServeUnroll = 4;
+constexpr int kServeBigBlock = 512;   // threads of the launch and of the long-tile phase
+constexpr int kServeBigUnroll = 4;
+constexpr int kServeCopies = 4;
+constexpr size_t kServeSmem =
+    sizeof(LargePlanes<kServeBigBlock / 32, kServeCopies>) > (size_t)kServeBlock * kSChunks * sizeof(long long)
+        ? sizeof(LargePlanes<kServeBigBlock / 32, kServeCopies>)
+        : (size_t)kServeBlock * kSChunks * sizeof(long long);
 
 // L2 prefetch of the 16-byte-aligned part of [p, q), in pieces of at most 64 KB.
 __device__ __forceinline__ void serve_prefetch(const double* p, const double* q) {
@@ -80,11 +94,47 @@ __device__ __forceinline__ void serve_prefetch(const double* p, const double* q)
   }
 }
 
-// A block of BLOCK threads holds BLOCK / W independent work groups, each of
-// which claims tiles on its own (one warp by default: a group's tiles end
-// without waiting at a barrier for its slowest warp).
-template <int BLOCK, int W, int UNROLL>
-__global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
+// Last tile of a slot in a batch, one warp: round the slot once and clear it
+// (a finish or a one-shot sum) or keep its exact sum in canonical form (an
+// append). sc: 67 words of shared scratch.
+__device__ __forceinline__ void serve_slot_finish(const BatchArgs& a, const BatchItem& it, AccState* g,
+                                                  long long* sc) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long* gc = reinterpret_cast<unsigned long long*>(g->chunk);
+  __threadfence();
+  if (it.flags & 1u) {  // round once and clear the slot
+    const long long v0 = (long long)atomicExch(gc + lane, 0ull);
+    const long long v1 = (long long)atomicExch(gc + lane + 32, 0ull);
+    const long long v2 = lane < 3 ? (long long)atomicExch(gc + lane + 64, 0ull) : 0;
+    unsigned fl = 0u;
+    unsigned long long key = 0ull;
+    if (lane == 0) {
+      fl = atomicExch(&g->flags, 0u);
+      key = atomicExch(&g->nan_key, 0ull);
+      atomicExch(&g->ticket, 0u);
+    }
+    fl = __shfl_sync(kFull, fl, 0);
+    key = __shfl_sync(kFull, key, 0);
+    const unsigned long long r = warp_round(v0, v1, v2, fl, key, sc, 32);
+    if (lane == 0 && it.res_idx >= 0) a.results[it.res_idx] = r;
+  } else {  // keep the exact sum, in canonical form
+    long long v0 = (long long)__ldcg(gc + lane);
+    long long v1 = (long long)__ldcg(gc + lane + 32);
+    long long v2 = lane < 3 ? (long long)__ldcg(gc + lane + 64) : 0;
+    warp_normalize(v0, v1, v2, sc, 32);
+    gc[lane] = (unsigned long long)v0;
+    gc[lane + 32] = (unsigned long long)v1;
+    if (lane < 3) gc[lane + 64] = (unsigned long long)v2;
+    if (lane == 0) g->ticket = 0u;
+  }
+}
+
+// The small tiles [0, small_tiles), by the first BLOCK threads of the block
+// (BLOCK / W independent work groups, each of which claims tiles on its own:
+// one warp by default, so a group's tiles end without waiting at a barrier
+// for its slowest warp). smem_srv holds the BLOCK threads' accumulators.
+template <int BLOCK, int W, int UNROLL, bool WHOLE_BLOCK>
+__device__ __forceinline__ void serve_small_tiles(const BatchArgs& a, long long* smem_srv) {
   static_assert(W >= 32 && W % 32 == 0 && BLOCK % W == 0, "whole warps per group");
   constexpr int NG = BLOCK / W;
   // the thread that claims the next tile: warp 1 of the group, beside warp 0's
@@ -93,7 +143,6 @@ __global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
   // load groups between carry propagations inside a tile longer than 2040
   // values per thread (at most 2045 adds per thread with head, tail and padding)
   constexpr int kCarryGroups = (kCarryInterval - 4 - 2 * UNROLL) / (2 * UNROLL);
-  extern __shared__ __align__(16) long long smem_srv[];
   __shared__ long long g_sc[NG][kSChunks];  // rounding scratch
   __shared__ long long g_tile[NG];
   __shared__ int g_item[NG];
@@ -113,7 +162,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
   // barrier 1 + group)
   auto gsync = [&]() {
     if (W == 32) __syncwarp();
-    else if (NG == 1) __syncthreads();
+    else if (NG == 1 && WHOLE_BLOCK) __syncthreads();
     else asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(W) : "memory");
   };
   SmallThread T;
@@ -121,7 +170,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
   // Accumulators are cleared once and every merge clears the window of
   // chunks it read, so they are zero whenever a tile starts.
   for (int c = 0; c < kSChunks; ++c) T.acc[c * BLOCK] = 0;
-  const long long total = a.hdr->total_tiles;
+  const long long total = a.hdr->small_tiles;
   const int nitems = a.hdr->nitems;
   // the last item with tile0 <= t
   auto item_of = [&](long long t) -> int {
@@ -149,8 +198,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
     const long long t = s_tile;
     if (t >= total) break;
     const BatchItem it = a.items[s_item];
-    const long long first = (t - it.tile0) * a.tile_elems;
-    const long long end = min(first + a.tile_elems, it.n);
+    const long long first = (t - it.tile0) * it.tile_len;
+    const long long end = min(first + it.tile_len, it.n);
     T.reset();
     if (first < end)
       accumulate_range<BLOCK, UNROLL, true, true>(T, it.x, first, end, gt, W, kCarryGroups);
@@ -187,46 +236,135 @@ __global__ void __launch_bounds__(BLOCK, 1) k_serve_batch(BatchArgs a) {
       s_last = (atomicAdd(&g->ticket, 1u) == (unsigned)(it.slot_tiles - 1)) ? 1u : 0u;
     }
     gsync();
-    if (s_last && gwarp == 0) {
-      __threadfence();
-      if (it.flags & 1u) {  // round once and clear the slot
-        const long long v0 = (long long)atomicExch(gc + lane, 0ull);
-        const long long v1 = (long long)atomicExch(gc + lane + 32, 0ull);
-        const long long v2 = lane < 3 ? (long long)atomicExch(gc + lane + 64, 0ull) : 0;
-        unsigned fl = 0u;
-        unsigned long long key = 0ull;
-        if (lane == 0) {
-          fl = atomicExch(&g->flags, 0u);
-          key = atomicExch(&g->nan_key, 0ull);
-          atomicExch(&g->ticket, 0u);
-        }
-        fl = __shfl_sync(kFull, fl, 0);
-        key = __shfl_sync(kFull, key, 0);
-        const unsigned long long r = warp_round(v0, v1, v2, fl, key, sc, 32);
-        if (lane == 0 && it.res_idx >= 0) a.results[it.res_idx] = r;
-      } else {  // keep the exact sum, in canonical form
-        long long v0 = (long long)__ldcg(gc + lane);
-        long long v1 = (long long)__ldcg(gc + lane + 32);
-        long long v2 = lane < 3 ? (long long)__ldcg(gc + lane + 64) : 0;
-        warp_normalize(v0, v1, v2, sc, 32);
-        gc[lane] = (unsigned long long)v0;
-        gc[lane + 32] = (unsigned long long)v1;
-        if (lane < 3) gc[lane + 64] = (unsigned long long)v2;
-        if (lane == 0) g->ticket = 0u;
-      }
-    }
+    if (s_last && gwarp == 0) serve_slot_finish(a, it, g, sc);
     if (gt == kClaimer) {  // where the next tile lies, and its start into L2
       const long long tn = s_tile;
       if (tn < total) {
         const int in = item_of(tn);
         s_item = in;
         const BatchItem& nx = a.items[in];
-        const long long nf = (tn - nx.tile0) * a.tile_elems;
-        const long long ne = min(min(nf + a.tile_elems, nx.n), nf + 48LL * W);
+        const long long nf = (tn - nx.tile0) * nx.tile_len;
+        const long long ne = min(min(nf + nx.tile_len, nx.n), nf + 48LL * W);
         if (nf < ne) serve_prefetch(nx.x + nf, nx.x + ne);
       }
     }
     gsync();
+  }
+}
+
+// A batch: first the small tiles, by the first 384 threads (the other warps
+// wait at the barrier), then the long tiles, each by the whole block with one
+// large superaccumulator in the same shared memory (Large, Fig. 4): the block
+// adds the tile into the planes, flushes them into a 67-chunk partial
+// (clearing them for the next tile), adds that into the request's slot and
+// takes a ticket; the slot's last tile finishes it as above.
+template <int UNROLL>
+__global__ void __launch_bounds__(kServeBigBlock, 1) k_serve(BatchArgs a) {
+  constexpr int NW = kServeBigBlock / 32;
+  extern __shared__ __align__(16) long long smem_srv[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < kServeBlock) serve_small_tiles<kServeBlock, kServeGroup, kServeUnroll, false>(a, smem_srv);
+  const long long total = a.hdr->total_tiles;
+  if (a.hdr->small_tiles >= total) return;  // no long tile in this batch (uniform)
+  __syncthreads();  // the small tiles' shared memory is free
+  LargePlanes<NW, kServeCopies>& P = *reinterpret_cast<LargePlanes<NW, kServeCopies>*>(smem_srv);
+  __shared__ long long b_sum[kSChunks];  // rounding scratch of a slot's finish
+  __shared__ long long b_tile, b_next_tile;
+  __shared__ int b_item, b_next_item;
+  __shared__ unsigned b_flags;
+  __shared__ unsigned long long b_nkey;
+  constexpr int kClaimer = 32;  // warp 1 claims the next tile while its block adds the current one
+  large_init(P, tid, kServeBigBlock);
+  const LargeLane L = large_lane(P);
+  const int nitems = a.hdr->nitems;
+  auto item_of = [&](long long t) -> int {  // the last item with tile0 <= t
+    int lo_i = 0, hi_i = nitems;
+    while (hi_i - lo_i > 1) {
+      const int mid = (lo_i + hi_i) >> 1;
+      if (a.items[mid].tile0 <= t) lo_i = mid; else hi_i = mid;
+    }
+    return lo_i;
+  };
+  if (tid == 0) {
+    b_tile = (long long)atomicAdd(&a.hdr->cursor_big, 1ull);
+    if (b_tile < total) b_item = item_of(b_tile);
+    b_flags = 0u;
+    b_nkey = 0ull;
+  }
+  __syncthreads();
+  // Three barriers per tile: after the adds, after the flush, and after the
+  // partial has gone into the slot. The next tile is claimed and located, and
+  // its start prefetched, while the block adds the current one; the slot's
+  // ticket and its finish run in warp 0 while the other warps start the next
+  // tile.
+  for (;;) {
+    const long long t = b_tile;
+    if (t >= total) break;
+    const BatchItem it = a.items[b_item];
+    if (tid == kClaimer) {
+      const long long tn = (long long)atomicAdd(&a.hdr->cursor_big, 1ull);
+      b_next_tile = tn;
+      if (tn < total) {
+        const int in = item_of(tn);
+        b_next_item = in;
+        const BatchItem& nx = a.items[in];
+        const long long nf = (tn - nx.tile0) * nx.tile_len;
+        const long long ne = min(min(nf + nx.tile_len, nx.n), nf + 48LL * kServeBigBlock);
+        if (nf < ne) serve_prefetch(nx.x + nf, nx.x + ne);
+      }
+    }
+    const long long first = (t - it.tile0) * it.tile_len;
+    const long long end = min(first + it.tile_len, it.n);
+    LargeThread T;
+    if (first < end) large_range<kServeBigBlock, UNROLL>(L, T, it.x, first, end, tid);
+    {
+      const unsigned zp = __reduce_add_sync(kFull, T.zpos);
+      const unsigned zn = __reduce_add_sync(kFull, T.zneg);
+      const unsigned f = __reduce_or_sync(kFull, T.flags());
+      const unsigned long long key = warp_max_ull(T.nkey);
+      if (lane == 0) {
+        if (zp) atomicAdd(&P.zeros[0], zp);
+        if (zn) atomicAdd(&P.zeros[1], zn);
+        if (f) atomicOr(&b_flags, f);
+        if (key) atomicMax(&b_nkey, key);
+      }
+    }
+    __syncthreads();  // every add is done
+    large_flush<NW, kServeCopies, true>(P);
+    __syncthreads();  // every run is flushed (and its planes cleared)
+    AccState* g = a.slots + it.slot;
+    unsigned long long* gc = reinterpret_cast<unsigned long long*>(g->chunk);
+    if (tid < kSChunks) {
+      long long v = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        v += P.part[w][tid];
+        P.part[w][tid] = 0;
+      }
+      if (v != 0) atomicAdd(gc + tid, (unsigned long long)v);
+    }
+    if (tid < 2) P.zeros[tid] = 0u;
+    unsigned fl = 0u;
+    unsigned long long nk = 0ull;
+    if (tid == 0) {  // this tile's record, then the next tile becomes current
+      fl = b_flags | ((it.n > 0 && t == it.tile0) ? kFlagAny : 0u);
+      nk = b_nkey;
+      b_flags = 0u;
+      b_nkey = 0ull;
+      b_tile = b_next_tile;
+      b_item = b_next_item;
+    }
+    __syncthreads();  // the partial is in the slot; the next tile is current
+    if (warp == 0) {
+      unsigned last = 0u;
+      if (lane == 0) {
+        if (fl) atomicOr(&g->flags, fl);
+        if (nk) atomicMax(&g->nan_key, nk);
+        __threadfence();
+        last = (atomicAdd(&g->ticket, 1u) == (unsigned)(it.slot_tiles - 1)) ? 1u : 0u;
+      }
+      if (__shfl_sync(kFull, last, 0)) serve_slot_finish(a, it, g, b_sum);
+    }
   }
 }
 
@@ -360,29 +498,47 @@ void xs_server_s::launch(BatchSlot& b) {
     order.push_back({tot, kv.first});
   }
   std::sort(order.begin(), order.end());
+  // Small requests' tiles first (smallest groups first, so they finish early),
+  // then long requests' block-wide tiles (largest groups first); a slot's
+  // ticket counts both kinds.
+  const long long te = opt.tile_elems, lt = opt.long_tile;
+  auto is_long = [&](const Request* r) { return r->n >= (int64_t)opt.long_min; };
+  auto tiles_of = [&](const Request* r) {
+    const long long len = is_long(r) ? lt : te;
+    return std::max<long long>(1, (r->n + len - 1) / len);
+  };
   long long tile0 = 0;
   int ni = 0;
-  const long long te = opt.tile_elems;
-  for (auto& o : order) {
-    const std::vector<int>& g = by_slot[o.second];
-    int slot_tiles = 0;
-    for (int k : g) slot_tiles += (int)std::max<long long>(1, (b.reqs[k]->n + te - 1) / te);
-    const Request* last = b.reqs[g.back()];
-    const bool fin = last->finish;
-    for (int k : g) {
-      const Request* r = b.reqs[k];
-      BatchItem& it = b.h_items[ni++];
-      it.x = r->x;
-      it.n = r->n;
-      it.tile0 = tile0;
-      it.slot = r->slot;
-      it.slot_tiles = slot_tiles;
-      it.res_idx = fin ? g.back() : -1;
-      it.flags = fin ? 1u : 0u;
-      tile0 += std::max<long long>(1, (r->n + te - 1) / te);
+  long long small_tiles = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    // long tiles of the largest groups first, so the batch does not end on
+    // one large request that few blocks are left to share
+    if (pass == 1) std::reverse(order.begin(), order.end());
+    for (auto& o : order) {
+      const std::vector<int>& g = by_slot[o.second];
+      int slot_tiles = 0;
+      for (int k : g) slot_tiles += (int)tiles_of(b.reqs[k]);
+      const bool fin = b.reqs[g.back()]->finish;
+      for (int k : g) {
+        const Request* r = b.reqs[k];
+        if (is_long(r) != (pass == 1)) continue;
+        BatchItem& it = b.h_items[ni++];
+        it.x = r->x;
+        it.n = r->n;
+        it.tile0 = tile0;
+        it.tile_len = is_long(r) ? lt : te;
+        it.slot = r->slot;
+        it.slot_tiles = slot_tiles;
+        it.res_idx = fin ? g.back() : -1;
+        it.flags = fin ? 1u : 0u;
+        tile0 += tiles_of(r);
+      }
     }
+    if (pass == 0) small_tiles = tile0;
   }
   b.h_hdr->cursor = 0ull;
+  b.h_hdr->cursor_big = (unsigned long long)small_tiles;
+  b.h_hdr->small_tiles = small_tiles;
   b.h_hdr->total_tiles = tile0;
   b.h_hdr->nitems = ni;
   const size_t bytes = sizeof(BatchHeader) + (size_t)ni * sizeof(BatchItem);
@@ -395,8 +551,7 @@ void xs_server_s::launch(BatchSlot& b) {
   a.tile_elems = te;
   const long long g = std::max<long long>(1, std::min<long long>(grid, tile0));
   if (e == cudaSuccess) {
-    k_serve_batch<kServeBlock, kServeGroup, kServeUnroll>
-        <<<(unsigned)g, kServeBlock, (size_t)kServeBlock * kSChunks * sizeof(long long), b.stream>>>(a);
+    k_serve<kServeBigUnroll><<<(unsigned)g, kServeBigBlock, kServeSmem, b.stream>>>(a);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess)
@@ -507,8 +662,12 @@ xs_status xs_server_create(xs_server* out, const xs_server_options* opts) {
   if (o.streams == 0) o.streams = 3;
   if (o.max_batch == 0) o.max_batch = 256;
   if (o.tile_elems == 0) o.tile_elems = 1 << 16;
+  if (o.long_min == 0) o.long_min = 1 << 20;
+  if (o.long_tile == 0) o.long_tile = 1 << 20;
+  // a long tile's sums of significands stay below 2^79 per chunk (the planes hold 96 bits)
   if (o.budget_bytes < 0 || o.max_sessions < 1 || o.streams < 1 || o.streams > 16 ||
-      o.max_batch < 1 || o.tile_elems < 2 * kServeGroup || o.tile_elems > (1 << 26))
+      o.max_batch < 1 || o.tile_elems < 2 * kServeGroup || o.tile_elems > (1 << 26) || o.long_min < 0 ||
+      o.long_tile < 2 * kServeBigBlock || o.long_tile > (1 << 26))
     return set_error(XS_ERR_INVALID_VALUE);
   xs_server s = new xs_server_s();
   s->device = ctx->device;
@@ -526,13 +685,11 @@ xs_status xs_server_create(xs_server* out, const xs_server_options* opts) {
     delete s;
     return from_cuda(e);
   };
-  const size_t smem = (size_t)kServeBlock * kSChunks * sizeof(long long);
-  cudaError_t e = cudaFuncSetAttribute(k_serve_batch<kServeBlock, kServeGroup, kServeUnroll>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_serve<kServeBigUnroll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kServeSmem);
   int occ = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve_batch<kServeBlock, kServeGroup, kServeUnroll>,
-                                                      kServeBlock, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve<kServeBigUnroll>, kServeBigBlock, kServeSmem);
   if (e != cudaSuccess) return fail(e);
   s->grid = ctx->num_sms * std::max(1, occ);
   e = dev_alloc(&s->d_slots, (size_t)o.max_sessions * sizeof(AccState));

@@ -49,7 +49,8 @@ class xs_seg_options(ctypes.Structure):
 
 class xs_server_options(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("max_sessions", ctypes.c_int),
-                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("tile_elems", ctypes.c_int)]
+                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("tile_elems", ctypes.c_int),
+                ("long_min", ctypes.c_int), ("long_tile", ctypes.c_int)]
 
 
 class xs_request(ctypes.Structure):
@@ -463,8 +464,8 @@ def _result_dict(r: xs_result) -> dict:
 
 
 def xs_server_create(budget_bytes: int = 0, max_sessions: int = 0, streams: int = 0,
-                     max_batch: int = 0, tile_elems: int = 0) -> int:
-    o = xs_server_options(budget_bytes, max_sessions, streams, max_batch, tile_elems)
+                     max_batch: int = 0, tile_elems: int = 0, long_min: int = 0, long_tile: int = 0) -> int:
+    o = xs_server_options(budget_bytes, max_sessions, streams, max_batch, tile_elems, long_min, long_tile)
     h = _vp()
     _check(load().xs_server_create(ctypes.byref(h), ctypes.byref(o)), "xs_server_create")
     return h.value

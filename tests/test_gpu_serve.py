@@ -51,9 +51,16 @@ def random_range(rng, n_pool, big=False):
     return lo, lo + m
 
 
-def test_mix_matches_alone_and_oracle():
+# requests of at least long_min values are summed in block-wide tiles of
+# long_tile values with a large superaccumulator; the others by one-warp groups
+LONG_OPTS = [{}, {"long_min": 5000, "long_tile": 1024}, {"long_min": 1, "long_tile": 3001}]
+
+
+@pytest.mark.parametrize("long_opts", LONG_OPTS, ids=[str(o) for o in LONG_OPTS])
+def test_mix_matches_alone_and_oracle(long_opts):
     x, d = make_pool()
-    server = xsum.xs_server_create(budget_bytes=64 << 20, streams=3, max_batch=64, tile_elems=1 << 16)
+    server = xsum.xs_server_create(budget_bytes=64 << 20, streams=3, max_batch=64, tile_elems=1 << 16,
+                                   **long_opts)
     rng = np.random.default_rng(7)
     plan = []  # (kind, ranges)
     for k in range(120):
@@ -155,8 +162,9 @@ def test_wait_times_out_on_the_host():
     xsum.xs_server_destroy(server)
 
 
-@pytest.mark.parametrize("tile", [64, 3000, 1 << 20])
-def test_tile_sizes_and_carries_inside_a_tile(tile):
+@pytest.mark.parametrize("tile,long_tile", [(64, 0), (3000, 0), (1 << 20, 0), (0, 1024), (0, 3001),
+                                            (0, 1 << 20), (0, 1 << 22)])
+def test_tile_sizes_and_carries_inside_a_tile(tile, long_tile):
     """The smallest tile (64 values), an odd size, and tiles of 2^20 values,
     32,768 adds per thread of a one-warp group, where carries propagate inside
     the tile. Same-sign terms at the top of a chunk (the largest adds), a
@@ -169,7 +177,10 @@ def test_tile_sizes_and_carries_inside_a_tile(tile):
     x[1_000_000:2_000_000] |= np.uint64(1 << 63)
     x[rng.integers(0, n, 5000)] = 0
     d = to_device(x)
-    server = xsum.xs_server_create(streams=2, tile_elems=tile)
+    # long_tile: every request in block-wide tiles; a tile of 2^22 such terms
+    # carries out of a chunk's high word about 2^10 times
+    server = xsum.xs_server_create(streams=2, tile_elems=tile, long_min=1 if long_tile else 1 << 30,
+                                   long_tile=long_tile)
     r_all = xsum.xs_server_submit(server, d, n)
     r_neg = xsum.xs_server_submit(server, d[1_000_000:2_000_000], 1_000_000)
     sid = xsum.xs_server_open_session(server)
@@ -186,6 +197,10 @@ def test_tile_size_limits():
     for bad in (-5, 32, 63, 1 << 27):
         with pytest.raises(xsum.XsError) as e:
             xsum.xs_server_create(tile_elems=bad)
+        assert e.value.status == xsum.XS_ERR_INVALID_VALUE
+    for bad in ({"long_tile": 1000}, {"long_tile": 1 << 27}, {"long_min": -1}):
+        with pytest.raises(xsum.XsError) as e:
+            xsum.xs_server_create(**bad)
         assert e.value.status == xsum.XS_ERR_INVALID_VALUE
 
 
