@@ -60,6 +60,7 @@ KERNEL_SOURCES = {
     "k_dot_small": [DEVICE_BLOCKS, ("xs_kernels.cuh", None, None), ("xs_dot.cu", None, None),
                     PREFETCH_DEFAULTS],
     "k_sum_f32": [DEVICE_BLOCKS, ("xs_f32.cu", None, None), PREFETCH_DEFAULTS],
+    "k_serve": [DEVICE_BLOCKS, ("xs_serve.cu", None, "// Rounded value of a session accumulator")],
 }
 
 

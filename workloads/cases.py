@@ -5,7 +5,9 @@
 Cases: sum_cfg1 (the default method), small_cfg1 and large_cfg1 (each method
 explicitly), sum_cfg2a (2^28 doubles, full exponent range) and small_cfg2a (the same
 with the small method), mean_cfg1, dot_cfg1, norm2_cfg1, f32_2e8,
-seg_cfg3_5k (5,000 segments of the config-3 length law), seg_tiny (2,000,000
+seg_cfg3_5k (5,000 segments of the config-3 length law), serve_cfg4 (300 one-shot
+requests of the serving recipe, log-uniform 1e3..1e8 values from three value
+recipes, through one server), seg_tiny (2,000,000
 segments of 1..100 values). Inputs are generated on the device; the case prints
 its median CUDA-event time. This module only calls the library.
 """
@@ -22,7 +24,7 @@ if ROOT not in sys.path:
 
 
 CASES = ("sum_cfg1", "small_cfg1", "sum_cfg2a", "small_cfg2a", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1", "f32_2e8",
-         "seg_cfg3_5k", "seg_tiny")
+         "seg_cfg3_5k", "seg_tiny", "serve_cfg4")
 
 
 def build_case(name: str):
@@ -84,6 +86,26 @@ def build_case(name: str):
         so = torch.empty(lengths.size, dtype=torch.float64, device=dev)
         plan = xsum.xs_seg_plan_create(v.view(torch.float64), od, lengths.size, so)
         return (lambda: xsum.xs_seg_plan_launch(plan)), 8 * total, (v, od, so)
+    if name == "serve_cfg4":
+        R = 1 << 27
+        arena = torch.empty(3 * R, dtype=torch.int64, device=dev)
+        devgen.band(arena[:R], 3, 0, -40, 40)
+        devgen.band(arena[R:2 * R], 4, 0, -60, 60)
+        devgen.paired(arena[2 * R:], 5, 0)
+        rng = np.random.default_rng(7)
+        items, total = [], 0
+        for _ in range(300):
+            nn = int(np.exp(rng.uniform(np.log(1e3), np.log(1e8))))
+            o = int(rng.integers(0, R - nn)) + int(rng.integers(0, 3)) * R
+            items.append((0, 0, arena.data_ptr() + 8 * o, nn, 0))
+            total += nn
+        srv = xsum.xs_server_create(budget_bytes=40 << 30, streams=3)
+
+        def run():
+            ids, _ = xsum.xs_server_replay(srv, items)
+            for i in ids:
+                xsum.xs_server_wait(srv, i, 120_000_000_000)
+        return run, 8 * total, (arena,)
     raise SystemExit(f"unknown case {name}")
 
 
