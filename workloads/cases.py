@@ -99,7 +99,8 @@ def build_case(name: str):
             o = int(rng.integers(0, R - nn)) + int(rng.integers(0, 3)) * R
             items.append((0, 0, arena.data_ptr() + 8 * o, nn, 0))
             total += nn
-        srv = xsum.xs_server_create(budget_bytes=40 << 30, streams=3)
+        # one batch may take every request that is pending when it is formed
+        srv = xsum.xs_server_create(budget_bytes=40 << 30, streams=3, max_batch=1024)
 
         def run():
             ids, _ = xsum.xs_server_replay(srv, items)
