@@ -289,8 +289,8 @@ typedef struct xs_server_options {
   int max_batch;        /* requests per batch launch (0 = 256) */
   int tile_elems;       /* elements per work item of a one-warp group (64 .. 2^26; 0 = 65536) */
   int long_min;         /* requests of at least this many values are summed in block-wide tiles,
-                           one large superaccumulator per block (Large, Fig. 4); 0 = 2^20 */
-  int long_tile;        /* values per block-wide tile (1024 .. 2^26; 0 = 2^20) */
+                           one large superaccumulator per block (Large, Fig. 4); 0 = 2^18 */
+  int long_tile;        /* values per block-wide tile (1024 .. 2^26; 0 = 2^21) */
 } xs_server_options;
 
 /* xs_request.flags */

@@ -5,7 +5,8 @@
 Cases: sum_cfg1 (the default method), small_cfg1 and large_cfg1 (each method
 explicitly), sum_cfg2a (2^28 doubles, full exponent range) and small_cfg2a (the same
 with the small method), mean_cfg1, dot_cfg1, norm2_cfg1, f32_2e8,
-seg_cfg3_5k (5,000 segments of the config-3 length law), serve_cfg4 (300 one-shot
+seg_cfg3_5k (5,000 segments of the config-3 length law), seg_cfg3 (all
+100,000, 58 GB, default options), serve_cfg4 (300 one-shot
 requests of the serving recipe, log-uniform 1e3..1e8 values from three value
 recipes, through one server), seg_tiny (2,000,000
 segments of 1..100 values). Inputs are generated on the device; the case prints
@@ -24,7 +25,7 @@ if ROOT not in sys.path:
 
 
 CASES = ("sum_cfg1", "small_cfg1", "sum_cfg2a", "small_cfg2a", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1", "f32_2e8",
-         "seg_cfg3_5k", "seg_tiny", "serve_cfg4")
+         "seg_cfg3_5k", "seg_cfg3", "seg_tiny", "serve_cfg4")
 
 
 def build_case(name: str):
@@ -73,9 +74,11 @@ def build_case(name: str):
         o32 = torch.empty(1, dtype=torch.float32, device=dev)
         fd = f.view(torch.float32)
         return (lambda: xsum.xs_sum_f32_async(fd, m, o32)), 4 * m, (f,)
-    if name in ("seg_cfg3_5k", "seg_tiny"):
+    if name in ("seg_cfg3_5k", "seg_cfg3", "seg_tiny"):
         if name == "seg_cfg3_5k":
             lengths = gen.cfg3_lengths(0, 5000, 10 ** 6)
+        elif name == "seg_cfg3":
+            lengths = gen.cfg3_lengths(0, 100_000, 10 ** 6)
         else:
             lengths = np.random.default_rng(0).integers(1, 101, 2_000_000).astype(np.int64)
         off = gen.cfg3_offsets(lengths)
