@@ -153,6 +153,14 @@ xs_status xs_norm2_async(const double* d_x, int64_t n, double* d_out, void* stre
  * |sum| >= 2^128 - 2^103. d_values 4-byte aligned; *d_out is a device float;
  * n <= 2^39 (XS_ERR_INVALID_VALUE above). Asynchronous. */
 xs_status xs_sum_f32_async(const float* d_values, int64_t n, float* d_out, void* stream);
+/* The same sum with the method chosen (an xs_method): XS_METHOD_SMALL, the
+ * small superaccumulator per thread (sixteen unsigned sign-split chunks);
+ * XS_METHOD_LARGE, the large superaccumulator per block (one chunk per
+ * sign+exponent, 512, Large, Fig. 4, each lane of a warp adding into its own
+ * column of 32-bit words); XS_METHOD_AUTO, what xs_sum_f32_async uses (the large
+ * one from 2^27 values). Same bits whatever the method. */
+xs_status xs_sum_f32_method_async(const float* d_values, int64_t n, float* d_out, int method,
+                                  void* stream);
 
 /* Inexact plain FP64 sum (a comparison baseline only, NOT exact: the rounding
  * after each addition depends on the launch shape). Writes *d_out. */

@@ -202,6 +202,40 @@ struct F32Args {
   int prefetch;
 };
 
+// End of a block of a binary32 sum, after its chunks are in the grid
+// accumulator: the special-value record joins the grid's, and the last block
+// to finish rounds once and leaves the accumulator zeroed. All threads call it.
+__device__ __forceinline__ void f32_finish(const F32Args& a, unsigned f, unsigned long long nkey,
+                                           unsigned& s_last) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long* gc = reinterpret_cast<unsigned long long*>(a.g->chunk);
+  if (blockIdx.x == 0 && tid == 0 && a.n > 0) f |= kFlagAny;
+  f = __reduce_or_sync(kFull, f);
+  const unsigned long long key = warp_max_ull(nkey);
+  if (lane == 0) {
+    if (f) atomicOr(&a.g->flags, f);
+    if (key) atomicMax(&a.g->nan_key, key);
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&a.g->ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  __syncthreads();
+  if (!s_last || warp != 0) return;
+  __threadfence();
+  const long long v = lane < kF32Chunks ? (long long)atomicExch(gc + lane, 0ull) : 0;
+  unsigned fl = 0u;
+  unsigned long long nk = 0ull;
+  if (lane == 0) {
+    fl = atomicExch(&a.g->flags, 0u);
+    nk = atomicExch(&a.g->nan_key, 0ull);
+    atomicExch(&a.g->ticket, 0u);
+  }
+  fl = __shfl_sync(kFull, fl, 0);
+  nk = __shfl_sync(kFull, nk, 0);
+  const unsigned bits = warp_round32(v, fl, nk);
+  if (lane == 0) *reinterpret_cast<unsigned*>(a.out) = bits;
+}
+
 template <int BLOCK, int UNROLL>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_sum_f32(F32Args a) {
   extern __shared__ __align__(16) long long smem32[];
@@ -298,45 +332,222 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_sum_f32(F32Args a) {
     const long long top = warp_sum_ll((long long)T.top_pos - (long long)T.top_neg);
     if (lane == 0 && top) atomicAdd(gc + 8, (unsigned long long)top);
   }
-  unsigned f = T.flags();
-  if (blockIdx.x == 0 && tid == 0 && a.n > 0) f |= kFlagAny;
-  f = __reduce_or_sync(kFull, f);
-  const unsigned long long key = warp_max_ull(T.nkey);
-  if (lane == 0) {
-    if (f) atomicOr(&a.g->flags, f);
-    if (key) atomicMax(&a.g->nan_key, key);
+  f32_finish(a, T.flags(), T.nkey, s_last);
+}
+
+// The paper's large superaccumulator for floats (Large, Fig. 4): one chunk per
+// sign+exponent, 512 of them, each a 64-bit sum of 24-bit significands held as
+// a 32-bit low word, added with an atomic that returns the old value, and a
+// 32-bit high word that counts the carries out of it (one per 256 or more adds
+// to that word). Every lane of a warp owns its own column of the planes,
+// [chunk][lane], so the 32 atomics of a warp instruction always fall in 32
+// different banks and never on one address, whatever the data; the warps of a
+// block share the columns. A term always adds its implicit bit; zeros and
+// subnormals are counted by sign and their implicit bits taken off at the
+// flush, Inf and NaN land in chunks 255 and 511, which the flush ignores. The
+// flush transfers chunk (s, e) = V * 2^(max(e, 1) - 150) into the signed chunks
+// of the grid accumulator (chunk i weighs 2^(32 i - 150)).
+constexpr int kF32LChunks = 512;
+struct F32Planes {
+  unsigned lo[kF32LChunks * 32];
+  unsigned hi[kF32LChunks * 32];
+  long long part[kF32Chunks + 1];  // the block's partial
+  unsigned zeros[2];               // zero/subnormal terms of the block, by sign
+};
+
+template <int BLOCK, int UNROLL>
+__global__ void __launch_bounds__(BLOCK, 1) k_sum_f32_large(F32Args a) {
+  extern __shared__ __align__(16) unsigned char smem32l[];
+  F32Planes& P = *reinterpret_cast<F32Planes*>(smem32l);
+  __shared__ unsigned s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {
+    uint4* w = reinterpret_cast<uint4*>(P.lo);
+    for (int k = tid; k < 2 * kF32LChunks * 32 / 4; k += BLOCK) w[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid <= kF32Chunks) P.part[tid] = 0;
+    if (tid < 2) P.zeros[tid] = 0u;
   }
-  __threadfence();
+  // this lane's column of the lo plane; chunk ix is at + ix * 128 bytes, its
+  // hi word at + 64 KB
+  const unsigned col = (unsigned)__cvta_generic_to_shared(P.lo) + 4u * (unsigned)lane;
+  constexpr unsigned kHiOff = 4u * kF32LChunks * 32;
+  const int head = (int)min((long long)((256u - ((uintptr_t)a.x & 255u)) & 255u) / 4, a.n);
+  const long long nq = (a.n - head) / 4;
+  const int tail = (int)((a.n - head) - nq * 4);
+  const uint4* xq = reinterpret_cast<const uint4*>(a.x + head);
+  const unsigned* xb = reinterpret_cast<const unsigned*>(a.x);
+  unsigned notnegz = 0u, sflags = 0u, zpos = 0u, zneg = 0u;
+  unsigned long long nkey = 0ull;
+  auto add = [&](unsigned b) {  // any term
+    const unsigned M = (b & 0x7FFFFFu) | 0x800000u;
+    const unsigned addr = col + ((b >> 23) << 7);
+    unsigned old;
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(M));
+    if (old + M < M) asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr + kHiOff));
+  };
+  auto record = [&](unsigned b) {  // the record of a term (rare path and ends)
+    const unsigned e = (b >> 23) & 0xFFu;
+    notnegz |= (b != kF32NegZero) ? 1u : 0u;
+    if (e == 0u) {
+      if (b >> 31) ++zneg; else ++zpos;
+    } else if (e == 0xFFu) {
+      if (b & 0x7FFFFFu) {
+        const unsigned long long k = nan32_key(b);
+        nkey = k > nkey ? k : nkey;
+      } else {
+        sflags |= (b >> 31) ? kFlagNegInf : kFlagPosInf;
+      }
+    }
+  };
   __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&a.g->ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
-  __syncthreads();
-  if (!s_last || warp != 0) return;
-  __threadfence();
-  const long long v = lane < kF32Chunks ? (long long)atomicExch(gc + lane, 0ull) : 0;
-  unsigned fl = 0u;
-  unsigned long long nk = 0ull;
-  if (lane == 0) {
-    fl = atomicExch(&a.g->flags, 0u);
-    nk = atomicExch(&a.g->nan_key, 0ull);
-    atomicExch(&a.g->ticket, 0u);
+  grid_dependency_wait();
+  if (blockIdx.x == 0 && tid < 32) {  // at most 2 head terms per lane, 3 tail terms in lane 0
+    for (int k = tid; k < head; k += 32) {
+      add(xb[k]);
+      record(xb[k]);
+    }
+    if (tid == 0)
+      for (int k = 0; k < tail; ++k) {
+        add(xb[a.n - 1 - k]);
+        record(xb[a.n - 1 - k]);
+      }
   }
-  fl = __shfl_sync(kFull, fl, 0);
-  nk = __shfl_sync(kFull, nk, 0);
-  const unsigned bits = warp_round32(v, fl, nk);
-  if (lane == 0) *reinterpret_cast<unsigned*>(a.out) = bits;
+  constexpr long long TQ = (long long)BLOCK * UNROLL;
+  const long long ntiles = (nq + TQ - 1) / TQ;
+  const long long G = gridDim.x;
+  auto load = [&](long long t, uint4* buf) {
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const long long q = t * TQ + (long long)u * BLOCK + tid;
+      if (q < nq) {
+        const ulonglong2 w = ld_stream(reinterpret_cast<const ulonglong2*>(xq + q));
+        buf[u] = make_uint4((unsigned)w.x, (unsigned)(w.x >> 32), (unsigned)w.y, (unsigned)(w.y >> 32));
+      } else {  // padding with -0: counted as a zero by the record, so its implicit bits are
+                // taken off at the flush, and it leaves the -0 record alone
+        buf[u] = make_uint4(kF32NegZero, kF32NegZero, kF32NegZero, kF32NegZero);
+      }
+    }
+  };
+  auto group = [&](const uint4* v) {
+    unsigned mx = 0u;
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+      mx = max(mx, ((v[k].x >> 23) & 0xFFu) - 1u);
+      mx = max(mx, ((v[k].y >> 23) & 0xFFu) - 1u);
+      mx = max(mx, ((v[k].z >> 23) & 0xFFu) - 1u);
+      mx = max(mx, ((v[k].w >> 23) & 0xFFu) - 1u);
+      add(v[k].x);
+      add(v[k].y);
+      add(v[k].z);
+      add(v[k].w);
+    }
+    if (__builtin_expect(mx < 0xFEu, 1)) {
+      notnegz = 1u;
+      return;
+    }
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+      record(v[k].x);
+      record(v[k].y);
+      record(v[k].z);
+      record(v[k].w);
+    }
+  };
+  long long t = blockIdx.x;
+  uint4 A[UNROLL], B[UNROLL];
+  if (t < ntiles) load(t, A);
+  while (t < ntiles) {
+    if (t + G < ntiles) load(t + G, B);
+    group(A);
+    t += G;
+    if (t >= ntiles) break;
+    if (t + G < ntiles) load(t + G, A);
+    group(B);
+    t += G;
+  }
+  grid_launch_dependents();
+  {
+    const unsigned zp = __reduce_add_sync(kFull, zpos), zn = __reduce_add_sync(kFull, zneg);
+    if (lane == 0) {
+      if (zp) atomicAdd(&P.zeros[0], zp);
+      if (zn) atomicAdd(&P.zeros[1], zn);
+    }
+  }
+  __syncthreads();
+  // flush: warp w takes chunks w, w + BLOCK / 32, ...; a chunk's 32 columns
+  // sum to V < 2^45 (at most 2^39 terms of < 2^24 in all)
+  for (int c = warp; c < kF32LChunks; c += BLOCK / 32) {
+    const unsigned e = (unsigned)c & 0xFFu;
+    long long v = (long long)(((unsigned long long)P.hi[c * 32 + lane] << 32) | P.lo[c * 32 + lane]);
+    if (!__any_sync(kFull, v != 0)) continue;
+    v = warp_sum_ll(v);
+    if (e == 0xFFu) continue;  // Inf / NaN record only
+    if (e == 0u) v -= (long long)P.zeros[c >> 8] << 23;  // the zeros' implicit bits
+    if (lane == 0 && v != 0) {
+      const unsigned ee = e ? e : 1u;
+      const unsigned __int128 W = (unsigned __int128)(unsigned long long)v << (ee & 31u);
+      const int i = (int)(ee >> 5);
+      const bool neg = (c >> 8) != 0;
+      unsigned long long* bp = reinterpret_cast<unsigned long long*>(P.part);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const long long piece = (long long)(unsigned)(W >> (32 * j));
+        if (piece) atomicAdd(bp + i + j, (unsigned long long)(neg ? -piece : piece));
+      }
+    }
+  }
+  __syncthreads();
+  unsigned long long* gc = reinterpret_cast<unsigned long long*>(a.g->chunk);
+  if (tid < kF32Chunks && P.part[tid] != 0) atomicAdd(gc + tid, (unsigned long long)P.part[tid]);
+  f32_finish(a, sflags | (notnegz ? kFlagNotNegZero : 0u), nkey, s_last);
 }
 
 namespace {
 constexpr int kF32Block = 1024;  // one block per SM: measured 4.5 % faster than two of 512
 constexpr int kF32Unroll = 3;  // 137.9 us on 2e8 floats back to back (2: 141.9; 4 spills)
+// The large superaccumulator: 128 KB of planes, one block of 1024 threads per
+// SM, three loads per thread. Measured on 2e8 floats back to back, against
+// the small one: 139.4 / 139.4 us on 2^U(-60,60), 133-135 / 138 us on U(-1,1),
+// N(0,1) and a constant, 186 / 268 us over the full exponent range (768 x 4:
+// 139, 132-134, 210; 512 x 4: 149, 141-144, 247). Its fixed cost is about
+// 5 us more (16.9 / 11.6 us at 2^22 floats, 99.2 / 97.0 at 2^27), so it is the
+// default from 2^27 values.
+constexpr int kF32LBlock = 1024;
+constexpr int kF32LUnroll = 3;
+constexpr long long kF32LargeMin = 1ll << 27;
 }  // namespace
 
 }  // namespace xs
 
 using namespace xs;
 
-extern "C" xs_status xs_sum_f32_async(const float* d_values, int64_t n, float* d_out,
-                                      void* stream) {
+namespace xs {
+namespace {
+// One wave of `kernel` (BLOCK threads, UNROLL vectors per thread per tile);
+// ID names the kernel for the once-per-device shared-memory attribute.
+template <int ID, class K>
+xs_status f32_launch(DeviceCtx* ctx, K kernel, int block, int unroll, size_t smem, const F32Args& a,
+                     cudaStream_t s) {
+  static bool attr[64] = {};  // per device
+  if (ctx->device < 64 && !attr[ctx->device]) {
+    XS_TRY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr[ctx->device] = true;
+  }
+  int occ = 1;
+  XS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem));
+  const long long tq = (long long)block * unroll;
+  const long long ntiles = std::max<long long>(1, (a.n / 4 + tq - 1) / tq);
+  const long long g =
+      std::max<long long>(1, std::min<long long>((long long)ctx->num_sms * std::max(1, occ), ntiles));
+  XS_TRY_CUDA(launch_pdl(kernel, (unsigned)g, (unsigned)block, smem, s, a));
+  return set_error(XS_OK);
+}
+}  // namespace
+}  // namespace xs
+
+extern "C" xs_status xs_sum_f32_method_async(const float* d_values, int64_t n, float* d_out,
+                                             int method, void* stream) {
+  if (method < XS_METHOD_AUTO || method > XS_METHOD_LARGE) return set_error(XS_ERR_INVALID_VALUE);
   if (n < 0 || n > (int64_t(1) << 39)) return set_error(XS_ERR_INVALID_VALUE);
   xs_status st = check_device_ptr(d_out);
   if (st != XS_OK) return st;
@@ -353,18 +564,6 @@ extern "C" xs_status xs_sum_f32_async(const float* d_values, int64_t n, float* d
   Workspace* w = workspace(ctx, s, &st);
   if (!w) return st;
   static_assert(sizeof(AccState32) <= sizeof(AccState), "fits the workspace accumulator");
-  const size_t smem = (size_t)kF32Block * 16 * sizeof(long long);
-  static bool attr[64] = {};
-  if (ctx->device < 64 && !attr[ctx->device]) {
-    XS_TRY_CUDA(cudaFuncSetAttribute(k_sum_f32<kF32Block, kF32Unroll>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr[ctx->device] = true;
-  }
-  int occ = 1;
-  XS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sum_f32<kF32Block, kF32Unroll>,
-                                                            kF32Block, smem));
-  const long long tq = (long long)kF32Block * kF32Unroll;
-  const long long ntiles = std::max<long long>(1, (n / 4 + tq - 1) / tq);
   F32Args a;
   a.x = d_values;
   a.n = n;
@@ -372,9 +571,17 @@ extern "C" xs_status xs_sum_f32_async(const float* d_values, int64_t n, float* d
   a.out = d_out;
   a.carry_tiles = std::max(1, (kF32CarryInterval - 7) / (4 * kF32Unroll));
   a.prefetch = prefetch_tiles(kF32Prefetch);
-  const long long g = std::max<long long>(1, std::min<long long>((long long)ctx->num_sms * std::max(1, occ), ntiles));
-  XS_TRY_CUDA(launch_pdl(k_sum_f32<kF32Block, kF32Unroll>, (unsigned)g, (unsigned)kF32Block, smem, s, a));
-  return set_error(XS_OK);
+  const bool large = method == XS_METHOD_LARGE || (method == XS_METHOD_AUTO && n >= kF32LargeMin);
+  if (large)
+    return f32_launch<1>(ctx, k_sum_f32_large<kF32LBlock, kF32LUnroll>, kF32LBlock, kF32LUnroll,
+                         sizeof(F32Planes), a, s);
+  return f32_launch<0>(ctx, k_sum_f32<kF32Block, kF32Unroll>, kF32Block, kF32Unroll,
+                       (size_t)kF32Block * 16 * sizeof(long long), a, s);
+}
+
+extern "C" xs_status xs_sum_f32_async(const float* d_values, int64_t n, float* d_out,
+                                      void* stream) {
+  return xs_sum_f32_method_async(d_values, n, d_out, XS_METHOD_AUTO, stream);
 }
 
 namespace xs {

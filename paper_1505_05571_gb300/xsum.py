@@ -98,6 +98,7 @@ _SIGS = {
     "xs_dot_async": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, _vp]),
     "xs_norm2_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_sum_f32_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
+    "xs_sum_f32_method_async": (ctypes.c_int, [_vp, _c_int64, _vp, ctypes.c_int, _vp]),
     "xs_acc_round_div": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_autotune_sum": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -309,6 +310,11 @@ def xs_norm2_async(d_x, n: int, d_out, stream=None) -> None:
 def xs_sum_f32_async(d_values, n: int, d_out, stream=None) -> None:
     _check(load().xs_sum_f32_async(_vals(d_values, n, 4), n, _ptr(d_out), _stream(stream)),
            "xs_sum_f32_async")
+
+
+def xs_sum_f32_method_async(d_values, n: int, d_out, method: int, stream=None) -> None:
+    _check(load().xs_sum_f32_method_async(_vals(d_values, n, 4), n, _ptr(d_out), method, _stream(stream)),
+           "xs_sum_f32_method_async")
 
 
 def xs_acc_round_div(h: int, divisor: int, d_out, stream=None) -> None:

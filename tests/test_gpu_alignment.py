@@ -67,9 +67,10 @@ def test_binary32_every_head_length(shift):
     assert t.data_ptr() % 256 == 0
     o32 = torch.empty(1, dtype=torch.float32, device="cuda")
     for n in (1, 3, 63, 64, 65, 99_999):
-        xsum.xs_sum_f32_async(t[shift:].view(torch.float32), n, o32)
-        got = int(o32.view(torch.int32).cpu().numpy().view(np.uint32)[0])
-        assert got == c_oracle.sum_f32_bits(h[shift:shift + n]), (shift, n)
+        for m in (xsum.XS_METHOD_SMALL, xsum.XS_METHOD_LARGE):
+            xsum.xs_sum_f32_method_async(t[shift:].view(torch.float32), n, o32, m)
+            got = int(o32.view(torch.int32).cpu().numpy().view(np.uint32)[0])
+            assert got == c_oracle.sum_f32_bits(h[shift:shift + n]), (shift, n, m)
 
 
 def test_segments_and_served_requests_at_every_offset(pool):
