@@ -503,8 +503,25 @@ void xs_server_s::launch(BatchSlot& b) {
   // ticket counts both kinds.
   const long long te = opt.tile_elems, lt = opt.long_tile;
   auto is_long = [&](const Request* r) { return r->n >= (int64_t)opt.long_min; };
+  // Long requests' tiles: long_tile values, unless the batch's long requests
+  // then make fewer tiles than there are blocks (a light load); the tiles are
+  // then shortened (to at least 2^16 values, a multiple of 4096) so that the
+  // batch still spreads over every block, and a lone mid-size request is not
+  // one block's work.
+  long long long_values = 0, long_tiles_full = 0;
+  for (const Request* r : b.reqs)
+    if (is_long(r)) {
+      long_values += r->n;
+      long_tiles_full += (r->n + lt - 1) / lt;
+    }
+  long long long_len = lt;
+  if (long_tiles_full < grid && long_values > 0) {
+    const long long want = ((long_values + grid - 1) / grid + 4095) / 4096 * 4096;
+    long_len = std::min(lt, std::max<long long>(std::min<long long>(lt, 1 << 16), want));
+  }
+  auto len_of = [&](const Request* r) -> long long { return is_long(r) ? long_len : te; };
   auto tiles_of = [&](const Request* r) {
-    const long long len = is_long(r) ? lt : te;
+    const long long len = len_of(r);
     return std::max<long long>(1, (r->n + len - 1) / len);
   };
   long long tile0 = 0;
@@ -526,7 +543,7 @@ void xs_server_s::launch(BatchSlot& b) {
         it.x = r->x;
         it.n = r->n;
         it.tile0 = tile0;
-        it.tile_len = is_long(r) ? lt : te;
+        it.tile_len = len_of(r);
         it.slot = r->slot;
         it.slot_tiles = slot_tiles;
         it.res_idx = fin ? g.back() : -1;
