@@ -245,10 +245,10 @@ typedef struct xs_seg_options {
   int block;         /* threads per work group of a long-segment tile: 128, 192, 256 or 384
                         with unroll 4; 32, 64, 128 or 192 with unroll 8. Groups smaller than
                         384 threads share one 384-thread block (twelve groups of one warp,
-                        six of two, three of 128, two of 192); default 32, one warp */
+                        six of two, three of 128, two of 192); default 64, two warps */
   int unroll;        /* 16-byte loads per thread per load group; default 8 */
   int tile_elems;    /* elements per work item of a long segment (2 x block .. 2^26);
-                        default 2^15 */
+                        default 2^18 */
   int short_max;     /* segments up to this length (at most 65,280) are summed by one warp;
                         default 4096 */
   int carry_tiles;   /* load groups (2 x unroll adds per thread each) between per-thread carry

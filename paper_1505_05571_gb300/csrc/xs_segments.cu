@@ -570,15 +570,17 @@ int seg_max_carry_groups(int unroll) { return (kCarryInterval - 4 - 2 * unroll) 
 xs_seg_options default_seg_options(DeviceCtx* ctx) {
   if (ctx->have_tuned_seg) return ctx->tuned_seg;
   xs_seg_options o;
-  // measured on GB300 over the config-3 length law (100,000 segments, 58 GB):
-  // one-warp groups of 32 x 8 with tiles of 2^15 values 10.09 ms, 64 x 8 with
-  // 2^16 10.85 ms, 128 x 8 with 2^17 11.11 ms, 192 x 8 11.53 ms. Independent
-  // warps end their tiles without waiting for one another; uniform segments of
-  // 10^7 values favour 128 x 8 (5.4 against 5.2 TB/s) -- xs_autotune_segments
-  // picks per workload
-  o.block = 32;
+  // measured on GB300 over the config-3 length law (100,000 segments, 58 GB),
+  // with the streamed bodies on 256-byte boundaries: groups of two warps x 8
+  // loads with tiles of 2^18 values and short_max 4096 take 9.53 ms (what the
+  // autotuner picks); one-warp groups with tiles of 2^15, 10.54 ms (before the
+  // alignment change the latter was the fastest, 10.09 ms). By length class:
+  // segments up to 4096 values 0.25 ms (60,102 of them, 0.24 GB), 4097 up to
+  // 2^18 2.61 ms (14.9 GB), longer ones 6.93 ms (43.2 GB, 6.24 TB/s) --
+  // xs_autotune_segments picks per workload
+  o.block = 64;
   o.unroll = 8;
-  o.tile_elems = 1 << 15;
+  o.tile_elems = 1 << 18;
   o.short_max = 4096;
   o.carry_tiles = 0;
   return o;
