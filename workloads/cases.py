@@ -24,7 +24,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-CASES = ("sum_cfg1", "small_cfg1", "sum_cfg2a", "small_cfg2a", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1", "f32_2e8",
+CASES = ("sum_cfg1", "small_cfg1", "sum_cfg2a", "small_cfg2a", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1", "f32_2e8", "f32_small_2e8",
          "seg_cfg3_5k", "seg_cfg3", "seg_tiny", "serve_cfg4")
 
 
@@ -64,7 +64,7 @@ def build_case(name: str):
         devgen.band(y, 1, 0)
         yd = y.view(torch.float64)
         return (lambda: xsum.xs_dot_async(xd, yd, n, out)), 16 * n, (x, y)
-    if name == "f32_2e8":
+    if name in ("f32_2e8", "f32_small_2e8"):
         m = 2 * 10 ** 8
         rng = np.random.default_rng(0)
         h = ((rng.integers(67, 187, m, dtype=np.uint32) << np.uint32(23))
@@ -73,6 +73,8 @@ def build_case(name: str):
         f = torch.from_numpy(h.view(np.int32)).to(dev)
         o32 = torch.empty(1, dtype=torch.float32, device=dev)
         fd = f.view(torch.float32)
+        if name == "f32_small_2e8":
+            return (lambda: xsum.xs_sum_f32_method_async(fd, m, o32, xsum.XS_METHOD_SMALL)), 4 * m, (f,)
         return (lambda: xsum.xs_sum_f32_async(fd, m, o32)), 4 * m, (f,)
     if name in ("seg_cfg3_5k", "seg_cfg3", "seg_tiny"):
         if name == "seg_cfg3_5k":
