@@ -158,7 +158,7 @@ xs_status xs_sum_f32_async(const float* d_values, int64_t n, float* d_out, void*
  * XS_METHOD_LARGE, the large superaccumulator per block (one chunk per
  * sign+exponent, 512, Large, Fig. 4, each lane of a warp adding into its own
  * column of 32-bit words); XS_METHOD_AUTO, what xs_sum_f32_async uses (the large
- * one from 2^27 values). Same bits whatever the method. */
+ * one from 5 x 2^24 values). Same bits whatever the method. */
 xs_status xs_sum_f32_method_async(const float* d_values, int64_t n, float* d_out, int method,
                                   void* stream);
 

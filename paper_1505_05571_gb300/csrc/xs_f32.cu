@@ -268,6 +268,15 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_sum_f32(F32Args a) {
     prefetch_l2(xq + first, (unsigned)(min(TQ, nq - first) * 16));
   };
   auto load = [&](long long t, uint4* buf) {
+    if ((t + 1) * TQ <= nq) {  // a full tile: no bounds checks (135.5 against 140.1 us on 2e8 floats)
+      const ulonglong2* p = reinterpret_cast<const ulonglong2*>(xq + t * TQ + tid);
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const ulonglong2 w = ld_stream(p + u * BLOCK);
+        buf[u] = make_uint4((unsigned)w.x, (unsigned)(w.x >> 32), (unsigned)w.y, (unsigned)(w.y >> 32));
+      }
+      return;
+    }
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
       const long long q = t * TQ + (long long)u * BLOCK + tid;
@@ -428,20 +437,27 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_f32_large(F32Args a) {
       }
     }
   };
+  // (b << 1) + 2^24 moves the exponent field to the top byte and adds one to
+  // it: exponent 255 wraps to a top byte of 0, exponent 0 gives 1, every
+  // normal term 2 or more, so the group is all normal exactly when the
+  // minimum is at least 2^25 (one shift-add and half a three-way minimum per
+  // term; measured 127 against 138 us on 2e8 floats with the exponent-field
+  // maximum)
   auto group = [&](const uint4* v) {
-    unsigned mx = 0u;
+    unsigned mn = 0xFFFFFFFFu;
 #pragma unroll
     for (int k = 0; k < UNROLL; ++k) {
-      mx = max(mx, ((v[k].x >> 23) & 0xFFu) - 1u);
-      mx = max(mx, ((v[k].y >> 23) & 0xFFu) - 1u);
-      mx = max(mx, ((v[k].z >> 23) & 0xFFu) - 1u);
-      mx = max(mx, ((v[k].w >> 23) & 0xFFu) - 1u);
+      mn = __vimin3_u32(mn, (v[k].x << 1) + 0x01000000u, (v[k].y << 1) + 0x01000000u);
+      mn = __vimin3_u32(mn, (v[k].z << 1) + 0x01000000u, (v[k].w << 1) + 0x01000000u);
+    }
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
       add(v[k].x);
       add(v[k].y);
       add(v[k].z);
       add(v[k].w);
     }
-    if (__builtin_expect(mx < 0xFEu, 1)) {
+    if (__builtin_expect(mn >= 0x02000000u, 1)) {
       notnegz = 1u;
       return;
     }
@@ -504,17 +520,18 @@ __global__ void __launch_bounds__(BLOCK, 1) k_sum_f32_large(F32Args a) {
 
 namespace {
 constexpr int kF32Block = 1024;  // one block per SM: measured 4.5 % faster than two of 512
-constexpr int kF32Unroll = 3;  // 137.9 us on 2e8 floats back to back (2: 141.9; 4 spills)
+constexpr int kF32Unroll = 3;  // 135.5 us on 2e8 floats back to back (2: 154.8; 4 spills)
 // The large superaccumulator: 128 KB of planes, one block of 1024 threads per
-// SM, three loads per thread. Measured on 2e8 floats back to back, against
-// the small one: 139.4 / 139.4 us on 2^U(-60,60), 133-135 / 138 us on U(-1,1),
-// N(0,1) and a constant, 186 / 268 us over the full exponent range (768 x 4:
-// 139, 132-134, 210; 512 x 4: 149, 141-144, 247). Its fixed cost is about
-// 5 us more (16.9 / 11.6 us at 2^22 floats, 99.2 / 97.0 at 2^27), so it is the
-// default from 2^27 values.
+// SM, three loads per thread (768 x 4: 128.9 us, 1024 x 4: 139.3, 512 x 6:
+// 140.3). Measured on 2e8 floats back to back, against the small one:
+// 127.0 / 136.0 us on 2^U(-60,60), 122-123 / 135.5 us on U(-1,1) and N(0,1),
+// 120.6 / 134.9 on a constant, 183 / 255 us over the full exponent range. Its
+// fixed cost is about 5 us more (16.9 / 11.6 us at 2^22 floats); the two are
+// level at 2^26 (53.4 / 52.7 us) and the large one is ahead at 2^27 (90.4 /
+// 94.7 us), so it is the default from 5 x 2^24 values.
 constexpr int kF32LBlock = 1024;
 constexpr int kF32LUnroll = 3;
-constexpr long long kF32LargeMin = 1ll << 27;
+constexpr long long kF32LargeMin = 5ll << 24;
 }  // namespace
 
 }  // namespace xs

@@ -204,6 +204,37 @@ def test_tiles_longer_than_the_carry_interval(tile):
     assert e.value.status == xsum.XS_ERR_INVALID_VALUE
 
 
+@pytest.mark.parametrize("dist", ["band", "full_range", "paired", "specials"])
+def test_tiny_segments_one_lane_each(dist):
+    """Segments of 0..140 values: those of up to 128 are summed by one lane
+    each and rounded side by side, the longer ones (and lanes whose chunk
+    window is too wide) by the warp; every result against the oracle."""
+    rng = np.random.default_rng(11)
+    lengths = rng.integers(0, 141, 40_000).astype(np.int64)
+    lengths[rng.integers(0, lengths.size, 500)] = rng.integers(0, 3, 500)  # many of 0, 1, 2
+    off = W.cfg3_offsets(lengths)
+    n = int(off[-1])
+    if dist == "band":
+        vals = W.cfg3_values(6, 0, n)
+    elif dist == "full_range":
+        vals = W.cfg2a_full_range(6, 0, n)
+    elif dist == "paired":
+        vals = W.cfg2a_paired(6, 0, n)
+    else:
+        vals = W.cfg3_values(7, 0, n)
+        specials = np.array([0x7FF0000000000000, 0xFFF0000000000000, 0x7FF8000000000123,
+                             0xFFF4000000000001, 0x8000000000000000, 0x0000000000000001,
+                             0x800FFFFFFFFFFFFF, 0x7FEFFFFFFFFFFFFF], dtype=np.uint64)
+        sel = rng.integers(0, n, n // 50)
+        vals[sel] = specials[rng.integers(0, specials.size, sel.size)]
+    expect = c_oracle.segment_sums_bits(vals, off)
+    vd, od = to_device(vals), torch.from_numpy(off).cuda()
+    for opts in (None, {"block": 32, "unroll": 8, "short_max": 100}, {"block": 384, "unroll": 4, "short_max": 4096}):
+        got = run_plan(vd, od, lengths.size, opts)
+        bad = np.nonzero(got != expect)[0]
+        assert bad.size == 0, (opts, [(int(k), int(lengths[k]), hex(got[k]), hex(expect[k])) for k in bad[:5]])
+
+
 def test_golden_boundary_cases_as_short_segments():
     """Every hand-derived boundary case (ties to even, sticky bits from
     2^-1074, overflow at the midpoint below 2^1024, subnormal results, signed
