@@ -194,9 +194,11 @@ __global__ void __launch_bounds__(kPrepThreads) k_seg_fill(SegArgs a) {
 
 // Short segments of at most this many values are summed by one lane each
 // (at most 2047 adds between carry propagations). Measured, 2e6 segments of
-// 1..100 values: 0.888 ms (one warp per segment: 2.420 ms; a limit of 64:
-// 1.483 ms); 4e6 of 1..16: 0.567 ms (4.278 ms); the config-3 segments of up
-// to 4096 values: 0.233 ms (0.242 ms).
+// 1..100 values: 0.750 ms (one warp per segment: 2.418 ms; a limit of 64:
+// 1.483 ms; four loads in flight and no L2 prefetch: 0.889 ms); 4e6 of 1..16:
+// 0.571 ms (4.276 ms); the config-3 segments of up to 4096 values: 0.233 ms
+// (0.240 ms). Fetching the next claim's metadata during the current one
+// gained nothing and cost 30 % on the config-3 short segments.
 constexpr int kSegLaneMax = 128;
 static_assert(kSegLaneMax <= 2040, "lane sums skip carry propagation");
 constexpr int kPhase1Ahead = 48;  // values per thread of a tile prefetched before the block starts it
@@ -484,11 +486,19 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
             r = (unsigned long long)__double_as_longlong(
                 __dadd_rn(__longlong_as_double((long long)b0), __longlong_as_double((long long)b1)));
           } else {
+            if (L >= 32) prefetch_range(xb + mlo, xb + mhi);  // the rest of it into L2
             T.reset();
             T.one<BLOCK, true>(b0);
             if (L > 1) T.one<BLOCK, true>(b1);
             long long k = mlo + 2;
-            for (; k + 4 <= mhi; k += 4) {  // four loads in flight
+            for (; k + 8 <= mhi; k += 8) {  // eight loads in flight
+              unsigned long long c[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) c[u] = __ldg(xb + k + u);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) T.one<BLOCK, true>(c[u]);
+            }
+            for (; k + 4 <= mhi; k += 4) {
               const unsigned long long c0 = __ldg(xb + k), c1 = __ldg(xb + k + 1);
               const unsigned long long c2 = __ldg(xb + k + 2), c3 = __ldg(xb + k + 3);
               T.one<BLOCK, true>(c0);
