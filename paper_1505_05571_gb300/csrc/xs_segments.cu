@@ -194,10 +194,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_seg_fill(SegArgs a) {
 
 // Short segments of at most this many values are summed by one lane each
 // (at most 2047 adds between carry propagations). Measured, 2e6 segments of
-// 1..100 values: 0.750 ms (one warp per segment: 2.418 ms; a limit of 64:
-// 1.483 ms; four loads in flight and no L2 prefetch: 0.889 ms); 4e6 of 1..16:
-// 0.571 ms (4.276 ms); the config-3 segments of up to 4096 values: 0.233 ms
-// (0.240 ms). Fetching the next claim's metadata during the current one
+// 1..100 values: 0.667 ms (one warp per segment: 2.418 ms; a limit of 64:
+// 1.483 ms; every term through the general add: 0.750 ms; also four loads in
+// flight and no L2 prefetch: 0.889 ms); 4e6 of 1..16: 0.545 ms (4.276 ms);
+// the config-3 segments of up to 4096 values: 0.217 ms (0.240 ms). Fetching the next claim's metadata during the current one
 // gained nothing and cost 30 % on the config-3 short segments.
 constexpr int kSegLaneMax = 128;
 static_assert(kSegLaneMax <= 2040, "lane sums skip carry propagation");
@@ -491,12 +491,11 @@ __global__ void __launch_bounds__(SegShape<W>::block, 1) k_seg_main(SegArgs a) {
             T.one<BLOCK, true>(b0);
             if (L > 1) T.one<BLOCK, true>(b1);
             long long k = mlo + 2;
-            for (; k + 8 <= mhi; k += 8) {  // eight loads in flight
-              unsigned long long c[8];
+            for (; k + 8 <= mhi; k += 8) {  // eight loads in flight, one normal-term test
+              ulonglong2 c[4];
 #pragma unroll
-              for (int u = 0; u < 8; ++u) c[u] = __ldg(xb + k + u);
-#pragma unroll
-              for (int u = 0; u < 8; ++u) T.one<BLOCK, true>(c[u]);
+              for (int u = 0; u < 4; ++u) c[u] = make_ulonglong2(__ldg(xb + k + 2 * u), __ldg(xb + k + 2 * u + 1));
+              T.group<BLOCK, 4, true>(c);
             }
             for (; k + 4 <= mhi; k += 4) {
               const unsigned long long c0 = __ldg(xb + k), c1 = __ldg(xb + k + 1);
