@@ -59,6 +59,8 @@ KERNEL_SOURCES = {
                    ("xs_segments.cu", "xs_seg_options default_seg_options(", "xs_status resolve_options(")],
     "k_dot_small": [DEVICE_BLOCKS, ("xs_kernels.cuh", None, None), ("xs_dot.cu", None, None),
                     PREFETCH_DEFAULTS],
+    "k_dot_large": [DEVICE_BLOCKS, ("xs_kernels.cuh", None, None), ("xs_dot.cu", None, None),
+                    PREFETCH_DEFAULTS],
     "k_sum_f32": [DEVICE_BLOCKS, ("xs_f32.cu", None, None), PREFETCH_DEFAULTS],
     "k_serve": [DEVICE_BLOCKS, ("xs_serve.cu", None, "// Rounded value of a session accumulator")],
 }
@@ -431,11 +433,15 @@ def next_rows(torch, np, xsum, devgen, dev, stream, xd, n):
     yd = y.view(torch.float64)
     t = b2b_time(torch, stream, lambda: xsum.xs_dot_async(xd, yd, n, res, stream))
     ti = b2b_time(torch, stream, lambda: torch.dot(xd, yd))
-    r["dot_cfg1"] = {"us": round(t * 1000, 1), "gbs": gbs(16 * n, t),
+    ts = b2b_time(torch, stream, lambda: xsum.xs_dot_method_async(xd, yd, n, res, xsum.XS_METHOD_SMALL, stream))
+    r["dot_cfg1"] = {"us": round(t * 1000, 1), "gbs": gbs(16 * n, t), "method": "large",
+                     "small_method_us": round(ts * 1000, 1),
                      "inexact_torch_dot_us": round(ti * 1000, 1)}
     t = b2b_time(torch, stream, lambda: xsum.xs_norm2_async(xd, n, res, stream))
     ti = b2b_time(torch, stream, lambda: torch.dot(xd, xd))
-    r["norm2_cfg1"] = {"us": round(t * 1000, 1), "gbs": gbs(8 * n, t),
+    ts = b2b_time(torch, stream, lambda: xsum.xs_norm2_method_async(xd, n, res, xsum.XS_METHOD_SMALL, stream))
+    r["norm2_cfg1"] = {"us": round(t * 1000, 1), "gbs": gbs(8 * n, t), "method": "large",
+                       "small_method_us": round(ts * 1000, 1),
                        "inexact_torch_dot_us": round(ti * 1000, 1),
                        "bound": "fp64 multiply pipe (0.53 T/s measured: 189 us for 1e8 products)"}
     del y, yd

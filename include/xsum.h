@@ -145,6 +145,15 @@ xs_status xs_dot_async(const double* d_x, const double* d_y, int64_t n, double* 
 /* Exact squared norm: the sum of the rounded squares d_x[i] * d_x[i], rounded
  * once (same passage). */
 xs_status xs_norm2_async(const double* d_x, int64_t n, double* d_out, void* stream);
+/* The same two with the method chosen (an xs_method): XS_METHOD_SMALL, the
+ * products into per-thread small superaccumulators; XS_METHOD_LARGE, into one
+ * large superaccumulator per block (Large, Fig. 4); XS_METHOD_AUTO, what
+ * xs_dot_async and xs_norm2_async use (the large one from 2^21 values). Same
+ * bits whatever the method; XS_ERR_INVALID_VALUE for any other method. */
+xs_status xs_dot_method_async(const double* d_x, const double* d_y, int64_t n, double* d_out,
+                              int method, void* stream);
+xs_status xs_norm2_method_async(const double* d_x, int64_t n, double* d_out, int method,
+                                void* stream);
 
 /* Exact sum of binary32 values, rounded once to the nearest float, ties to
  * even -- the single-precision variant with a smaller superaccumulator

@@ -97,6 +97,8 @@ _SIGS = {
     "xs_mean_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_dot_async": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, _vp]),
     "xs_norm2_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
+    "xs_dot_method_async": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, ctypes.c_int, _vp]),
+    "xs_norm2_method_async": (ctypes.c_int, [_vp, _c_int64, _vp, ctypes.c_int, _vp]),
     "xs_sum_f32_async": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
     "xs_sum_f32_method_async": (ctypes.c_int, [_vp, _c_int64, _vp, ctypes.c_int, _vp]),
     "xs_acc_round_div": (ctypes.c_int, [_vp, _c_int64, _vp, _vp]),
@@ -305,6 +307,16 @@ def xs_dot_async(d_x, d_y, n: int, d_out, stream=None) -> None:
 
 def xs_norm2_async(d_x, n: int, d_out, stream=None) -> None:
     _check(load().xs_norm2_async(_vals(d_x, n), n, _ptr(d_out), _stream(stream)), "xs_norm2_async")
+
+
+def xs_dot_method_async(d_x, d_y, n: int, d_out, method: int, stream=None) -> None:
+    _check(load().xs_dot_method_async(_vals(d_x, n), _vals(d_y, n), n, _ptr(d_out), method,
+                                      _stream(stream)), "xs_dot_method_async")
+
+
+def xs_norm2_method_async(d_x, n: int, d_out, method: int, stream=None) -> None:
+    _check(load().xs_norm2_method_async(_vals(d_x, n), n, _ptr(d_out), method, _stream(stream)),
+           "xs_norm2_method_async")
 
 
 def xs_sum_f32_async(d_values, n: int, d_out, stream=None) -> None:

@@ -49,8 +49,10 @@ def test_dot_every_head_length(pool, shift):
     for n in SIZES:
         for yshift in (0, 1, 5):
             xs, ys = x[shift:shift + n], x[1000 + yshift:1000 + yshift + n]
-            xsum.xs_dot_async(d[shift:], d[1000 + yshift:], n, out)
-            assert int(bits_of(out)[0]) == products.dot_bits(xs, ys), (shift, yshift, n)
+            expect = products.dot_bits(xs, ys)
+            for m in (xsum.XS_METHOD_SMALL, xsum.XS_METHOD_LARGE):
+                xsum.xs_dot_method_async(d[shift:], d[1000 + yshift:], n, out, m)
+                assert int(bits_of(out)[0]) == expect, (shift, yshift, n, m)
 
 
 @pytest.mark.parametrize("shift", [0, 1, 2, 3, 17, 31, 32, 33, 62, 63, 64])

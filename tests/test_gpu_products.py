@@ -11,18 +11,41 @@ from tests.gpu_util import bits_of, out_slot, to_device
 pytestmark = pytest.mark.gpu
 
 
+METHODS = (xsum.XS_METHOD_SMALL, xsum.XS_METHOD_LARGE)
+
+
 def gpu_dot(x, y, mx=0, my=0):
+    """The dot product through the default entry point and through each
+    method; all of them must give the same bits, which are returned."""
     dx, dy = to_device(x, mx), to_device(y, my)
     out = out_slot()
     xsum.xs_dot_async(dx, dy, dx.numel(), out)
-    return int(bits_of(out)[0])
+    got = int(bits_of(out)[0])
+    for m in METHODS:
+        xsum.xs_dot_method_async(dx, dy, dx.numel(), out, m)
+        assert int(bits_of(out)[0]) == got, ("method", m, mx, my)
+    return got
 
 
 def gpu_norm2(x, mx=0):
     dx = to_device(x, mx)
     out = out_slot()
     xsum.xs_norm2_async(dx, dx.numel(), out)
-    return int(bits_of(out)[0])
+    got = int(bits_of(out)[0])
+    for m in METHODS:
+        xsum.xs_norm2_method_async(dx, dx.numel(), out, m)
+        assert int(bits_of(out)[0]) == got, ("method", m, mx)
+    return got
+
+
+def test_products_reject_unknown_methods():
+    dx = to_device(W.cfg1_band(2, 0, 100))
+    out = out_slot()
+    for bad in (-1, 3):
+        with pytest.raises(xsum.XsError):
+            xsum.xs_dot_method_async(dx, dx, 100, out, bad)
+        with pytest.raises(xsum.XsError):
+            xsum.xs_norm2_method_async(dx, 100, out, bad)
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 1537, 100_001, 3_000_003])

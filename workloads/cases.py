@@ -24,7 +24,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-CASES = ("sum_cfg1", "small_cfg1", "sum_cfg2a", "small_cfg2a", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1", "f32_2e8", "f32_small_2e8",
+CASES = ("sum_cfg1", "small_cfg1", "sum_cfg2a", "small_cfg2a", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1", "dot_small_cfg1", "norm2_small_cfg1", "f32_2e8", "f32_small_2e8",
          "seg_cfg3_5k", "seg_cfg3", "seg_tiny", "serve_cfg4")
 
 
@@ -45,7 +45,8 @@ def build_case(name: str):
         devgen.full_range(x, 0, 0)
         m = xsum.XS_METHOD_AUTO if name == "sum_cfg2a" else xsum.XS_METHOD_SMALL
         return (lambda: xsum.xs_sum_async(x.view(torch.float64), n, out, m)), 8 * n, (x,)
-    if name in ("sum_cfg1", "small_cfg1", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1"):
+    if name in ("sum_cfg1", "small_cfg1", "mean_cfg1", "large_cfg1", "dot_cfg1", "norm2_cfg1", "dot_small_cfg1",
+                "norm2_small_cfg1"):
         n = 10 ** 8
         x = torch.empty(n, dtype=torch.int64, device=dev)
         devgen.band(x, 0, 0)
@@ -60,9 +61,13 @@ def build_case(name: str):
             return (lambda: xsum.xs_sum_async(xd, n, out, xsum.XS_METHOD_LARGE)), 8 * n, (x,)
         if name == "norm2_cfg1":
             return (lambda: xsum.xs_norm2_async(xd, n, out)), 8 * n, (x,)
+        if name == "norm2_small_cfg1":
+            return (lambda: xsum.xs_norm2_method_async(xd, n, out, xsum.XS_METHOD_SMALL)), 8 * n, (x,)
         y = torch.empty(n, dtype=torch.int64, device=dev)
         devgen.band(y, 1, 0)
         yd = y.view(torch.float64)
+        if name == "dot_small_cfg1":
+            return (lambda: xsum.xs_dot_method_async(xd, yd, n, out, xsum.XS_METHOD_SMALL)), 16 * n, (x, y)
         return (lambda: xsum.xs_dot_async(xd, yd, n, out)), 16 * n, (x, y)
     if name in ("f32_2e8", "f32_small_2e8"):
         m = 2 * 10 ** 8
