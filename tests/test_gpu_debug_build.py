@@ -14,7 +14,7 @@ import sys
 import numpy as np
 import pytest
 
-from oracle import c_oracle
+from oracle import c_oracle, products
 from paper_1505_05571_gb300 import build
 
 pytestmark = pytest.mark.gpu
@@ -37,6 +37,11 @@ for name, bits in cases().items():
     for m in (xsum.XS_METHOD_AUTO, xsum.XS_METHOD_SMALL, xsum.XS_METHOD_LARGE):
         xsum.xs_sum_async(d, d.numel(), out, m)
         res[f"{name}/{m}"] = int(out.view(torch.int64).item()) & ((1 << 64) - 1)
+    if d.numel() <= 1 << 22:  # products: x against x reversed, both methods
+        dr = d.flip(0).contiguous()
+        for m in (xsum.XS_METHOD_SMALL, xsum.XS_METHOD_LARGE):
+            xsum.xs_dot_method_async(d, dr, d.numel(), out, m)
+            res[f"{name}/dot/{m}"] = int(out.view(torch.int64).item()) & ((1 << 64) - 1)
 vals, off = segmented()
 vd = torch.from_numpy(vals.view(np.int64)).cuda().view(torch.float64)
 od = torch.from_numpy(off).cuda()
@@ -66,6 +71,10 @@ def test_debug_build_matches_oracle_and_no_check_fails():
         expect = c_oracle.sum_bits(bits)
         for m in (0, 1, 2):
             assert got[f"{name}/{m}"] == expect, (name, m)
+        if bits.size <= 1 << 22:
+            expect_dot = products.dot_bits(bits, bits[::-1].copy())
+            for m in (1, 2):
+                assert got[f"{name}/dot/{m}"] == expect_dot, (name, "dot", m)
     vals, off = segmented()
     expect = [int(b) for b in c_oracle.segment_sums_bits(vals, off)]
     for k in range(3):
