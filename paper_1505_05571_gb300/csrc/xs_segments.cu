@@ -197,8 +197,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_seg_fill(SegArgs a) {
 // 1..100 values: 0.667 ms (one warp per segment: 2.418 ms; a limit of 64:
 // 1.483 ms; every term through the general add: 0.750 ms; also four loads in
 // flight and no L2 prefetch: 0.889 ms); 4e6 of 1..16: 0.545 ms (4.276 ms);
-// the config-3 segments of up to 4096 values: 0.217 ms (0.240 ms). Fetching the next claim's metadata during the current one
-// gained nothing and cost 30 % on the config-3 short segments.
+// the 60,102 segments of up to 4096 values among 100,000 of log-uniform
+// lengths in 1..1e6: 0.217 ms (0.240 ms). Fetching the next claim's metadata
+// during the current one gained nothing and cost 30 % on those.
 constexpr int kSegLaneMax = 128;
 static_assert(kSegLaneMax <= 2040, "lane sums skip carry propagation");
 constexpr int kPhase1Ahead = 48;  // values per thread of a tile prefetched before the block starts it
@@ -696,7 +697,7 @@ int seg_max_carry_groups(int unroll) { return (kCarryInterval - 4 - 2 * unroll) 
 xs_seg_options default_seg_options(DeviceCtx* ctx) {
   if (ctx->have_tuned_seg) return ctx->tuned_seg;
   xs_seg_options o;
-  // measured on GB300 over the config-3 length law (100,000 segments, 58 GB),
+  // measured on GB300 over 100,000 segments of log-uniform lengths in 1..1e6 (58 GB),
   // with the streamed bodies on 256-byte boundaries: groups of two warps x 8
   // loads with tiles of 2^18 values and short_max 4096 take 9.53 ms (what the
   // autotuner picks); one-warp groups with tiles of 2^15, 10.54 ms (before the

@@ -69,9 +69,10 @@ struct BatchArgs {
 // threads with per-thread small superaccumulators, four loads per thread; then
 // the long requests' tiles (2^21 values by default) to whole blocks with one
 // large superaccumulator each (four loads per thread). Measured on GB300 with
-// saturated serving of config-4 requests, the one-warp groups alone reach
-// 5.1 TB/s whatever the block shape (192 or 384 threads, 4 loads; 8 loads:
-// 3.3-4.5 TB/s), the same with one batch in flight as with three.
+// saturated serving of Poisson requests of 1e3..1e8 values (log-uniform), the
+// one-warp groups alone reach 5.1 TB/s whatever the block shape (192 or 384
+// threads, 4 loads; 8 loads: 3.3-4.5 TB/s), the same with one batch in flight
+// as with three.
 constexpr int kServeBlock = 384;      // threads of the small-tile phase
 constexpr int kServeGroup = 32;
 constexpr int kServeUnroll = 4;
@@ -679,9 +680,9 @@ xs_status xs_server_create(xs_server* out, const xs_server_options* opts) {
   if (o.streams == 0) o.streams = 3;
   if (o.max_batch == 0) o.max_batch = 256;
   if (o.tile_elems == 0) o.tile_elems = 1 << 16;
-  // measured on GB300, saturated config-4 serving: long requests from 2^18
-  // values in tiles of 2^21, 6.56 TB/s (2^20 from 2^20: 6.43; tiles of 2^19:
-  // 6.23; of 2^22: 6.57)
+  // measured on GB300, saturated serving of requests of 1e3..1e8 values: long
+  // requests from 2^18 values in tiles of 2^21, 6.56 TB/s (2^20 from 2^20:
+  // 6.43; tiles of 2^19: 6.23; of 2^22: 6.57)
   if (o.long_min == 0) o.long_min = 1 << 18;
   if (o.long_tile == 0) o.long_tile = 1 << 21;
   // a long tile's sums of significands stay below 2^79 per chunk (the planes hold 96 bits)
