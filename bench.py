@@ -17,6 +17,7 @@ path); rank 0 prints the whole-job throughput over the slowest rank.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -653,12 +654,20 @@ def run_ours(args):
     e2e_steps = max(3, min(args.steps, 50))  # about 0.2 s: one stall of the shared host link weighs less
     torch.cuda.synchronize(dev)
     t_calls = []
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        tc = time.perf_counter()
-        r = xsum.xs_sum_host(hd, n, stream)
-        t_calls.append(time.perf_counter() - tc)
-    t_e2e = max_over_ranks(torch, (time.perf_counter() - t0) / e2e_steps, dev)
+    # no Python garbage collection inside the host-timed loop: after the other
+    # configurations a collection can pause the interpreter for tens of ms
+    gc.collect()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            tc = time.perf_counter()
+            r = xsum.xs_sum_host(hd, n, stream)
+            t_calls.append(time.perf_counter() - tc)
+        t_e2e_local = (time.perf_counter() - t0) / e2e_steps
+    finally:
+        gc.enable()
+    t_e2e = max_over_ranks(torch, t_e2e_local, dev)
     t_calls.sort()
     same = (np.array([r0, r]).view(np.int64) == bits_last).all()
     # the host link alone: one plain pinned H2D copy of the same 800 MB (no summation)

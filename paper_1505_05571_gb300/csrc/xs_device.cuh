@@ -334,6 +334,12 @@ struct SmallThread {
         continue;
       }
       notnegz |= (b != kNegZero) ? 1u : 0u;
+      if ((b << 1) == 0ull) {
+        // a zero: the short path added 2^20 (+0) or -2^20 (-0) to chunk 1;
+        // take exactly that back, with no call to the general path
+        acc[BLOCK] -= (b >> 63) ? -(1ll << 20) : (1ll << 20);
+        continue;
+      }
       take_back<BLOCK>(acc, b);
       if (e == 0x7FFu) special(b);
     }

@@ -106,11 +106,24 @@ struct SmallThread32 {
     } else {
 #pragma unroll
       for (int k = 0; k < U; ++k) {
-        one<BLOCK>(v[k].x);
-        one<BLOCK>(v[k].y);
-        one<BLOCK>(v[k].z);
-        one<BLOCK>(v[k].w);
+        rare<BLOCK>(v[k].x);
+        rare<BLOCK>(v[k].y);
+        rare<BLOCK>(v[k].z);
+        rare<BLOCK>(v[k].w);
       }
+    }
+  }
+  // A term of a group that holds a zero, subnormal, Inf or NaN: normal terms
+  // take the short path, zeros add nothing, the rest the general one.
+  template <int BLOCK>
+  __device__ __forceinline__ void rare(unsigned b) {
+    if (((b >> 23) & 0xFFu) - 1u < 0xFEu) {
+      notnegz = 1u;
+      add_normal<BLOCK>(b);
+    } else if ((b << 1) == 0u) {
+      notnegz |= (b != kF32NegZero) ? 1u : 0u;
+    } else {
+      one<BLOCK>(b);
     }
   }
   // Unsigned carry propagation of both chunk sets (small section), the carry
