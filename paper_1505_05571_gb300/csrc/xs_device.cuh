@@ -303,7 +303,11 @@ struct SmallThread {
   // path. Between two carry propagations a chunk so holds at most the adds of
   // the terms seen, as without the detour. Groups padded with -0 (the ragged
   // end of a range) take the test-first form above instead.
-  template <int BLOCK, int U, bool TRACK = false>
+  // ZEROS: a zero is taken back in place (below) rather than by the general
+  // path. Both are exact; the segmented kernel's compiled loop was 0.9 %
+  // faster without it on its usual data (no zeros), so accumulate_range keeps
+  // the general path.
+  template <int BLOCK, int U, bool TRACK = false, bool ZEROS = true>
   __device__ __forceinline__ void group_spec(const ulonglong2* v) {
     unsigned mx = 0u, mn = 0x7FFu;
 #pragma unroll
@@ -334,7 +338,7 @@ struct SmallThread {
         continue;
       }
       notnegz |= (b != kNegZero) ? 1u : 0u;
-      if ((b << 1) == 0ull) {
+      if (ZEROS && (b << 1) == 0ull) {
         // a zero: the short path added 2^20 (+0) or -2^20 (-0) to chunk 1;
         // take exactly that back, with no call to the general path
         acc[BLOCK] -= (b >> 63) ? -(1ll << 20) : (1ll << 20);
@@ -424,12 +428,12 @@ __device__ __forceinline__ void accumulate_range(SmallThread& T, const double* x
   while (g < nfull) {
     prefetch(g + kAhead + 1);
     if (g + 1 < nfull) load_full(g + 1, B);
-    T.group_spec<BLOCK, UNROLL, TRACK>(A);
+    T.group_spec<BLOCK, UNROLL, TRACK, false>(A);
     tick();
     if (++g >= nfull) break;
     prefetch(g + kAhead + 1);
     if (g + 1 < nfull) load_full(g + 1, A);
-    T.group_spec<BLOCK, UNROLL, TRACK>(B);
+    T.group_spec<BLOCK, UNROLL, TRACK, false>(B);
     tick();
     ++g;
   }

@@ -138,6 +138,29 @@ def test_rare_terms_between_largest_chunk_adds(every):
     all_shapes_equal(y, c_oracle.sum_bits(y))
 
 
+@pytest.mark.parametrize("frac", [0.01, 0.1, 0.5, 0.97])
+def test_many_zeros_of_both_signs(frac):
+    """Zeros (+0 and -0) at random positions among band values: a zero in a
+    group of the speculative short path is taken back in place (its 2^20 in
+    chunk 1); every shape, aligned and not, against the oracle, and the same
+    values as floats through both binary32 methods."""
+    n = 1_000_003
+    rng = np.random.default_rng(int(frac * 1000))
+    x = W.cfg1_band(21, 0, n).copy()
+    sel = rng.random(n) < frac
+    x[sel] = np.where(rng.random(int(sel.sum())) < 0.5, np.uint64(0), np.uint64(0x8000000000000000))
+    all_shapes_equal(x, c_oracle.sum_bits(x), misalign=(0, 1))
+    f = x.view(np.float64).astype(np.float32)
+    f[sel] = np.where(x[sel] >> np.uint64(63), np.float32(-0.0), np.float32(0.0))
+    fb = f.view(np.uint32)
+    expect = c_oracle.sum_f32_bits(fb)
+    d = torch.from_numpy(fb.view(np.int32)).cuda().view(torch.float32)
+    o32 = torch.empty(1, dtype=torch.float32, device="cuda")
+    for m in (xsum.XS_METHOD_SMALL, xsum.XS_METHOD_LARGE):
+        xsum.xs_sum_f32_method_async(d, n, o32, m)
+        assert int(o32.view(torch.int32).cpu().numpy().view(np.uint32)[0]) == expect, (frac, m)
+
+
 def test_permutation_invariance():
     x = W.cfg2a_paired(2, 0, 500_000)
     expect = c_oracle.sum_bits(x)
