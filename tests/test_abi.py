@@ -117,6 +117,11 @@ def test_argument_errors_come_before_any_device_work(lib_path):
         (lambda: xsum.xs_acc_add(0, 0x1000, 10), E_PTR),        # null handle
         (lambda: xsum.xs_sum_f32_async(0x1000, -1, 0x2000), E_VAL),
         (lambda: xsum.xs_sum_f32_async(0x1000, (1 << 39) + 1, 0x2000), E_VAL),
+        (lambda: xsum.xs_sum_f32_method_async(0x1000, 10, 0x2000, 3), E_VAL),  # unknown method
+        (lambda: xsum.xs_dot_method_async(0x1000, 0x2000, 10, 0x3000, 3), E_VAL),
+        (lambda: xsum.xs_dot_method_async(0x1000, 0x2000, 10, 0x3000, -1), E_VAL),
+        (lambda: xsum.xs_norm2_method_async(0x1000, 10, 0x3000, 7), E_VAL),
+        (lambda: xsum.xs_dot_async(0x1000, 0x2000, -1, 0x3000), E_VAL),
     ]
     for k, (fn, want) in enumerate(cases):
         assert status_of(fn) == want, k
